@@ -1,0 +1,240 @@
+"""FP64 CPU oracle for slice-wise propagation (Herb & Welter, "Parallel time
+integration using Batched BLAS routines", arXiv 2108.07126).
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, plain reference that the
+CUDA library is checked against.  Only the test suite, the smoke check and the
+CPU-baseline leg of the benchmark may import it; the product path never does.
+It shares no code with the CUDA library (no kernels, headers, tables or
+helpers); the only thing both sides see is the seeded input arrays.
+
+What it computes, each piece following the paper's definitions:
+
+* ``hamiltonian``        -- H(t) = H0 + sum_k c_k(t) H_k          (Sec. 2, Eq. format_control)
+* ``slice_exponents``    -- the Hermitian exponent G_j of every slice, so that
+                            U_j = exp(-i G_j):
+    - midpoint rule      G_j = dt * H(t_j + dt/2)                 (Sec. 3.2 and Sec. 4: Omega_1 by the mid-point rule)
+    - Gauss-Legendre 4   G_j = dt/2 (H1 + H2) + i sqrt(3) dt^2/12 [H1, H2]
+                         with H1, H2 at t_j + dt (1/2 -+ sqrt(3)/6)   (Sec. 4, Eq. magnus: Omega_1 + Omega_2)
+    - Simpson 4          G_j = dt/6 (H1 + 4 H2 + H3) + i dt^2/12 [H1, H3]
+                         with H1, H2, H3 at t_j, t_j + dt/2, t_j + dt  (Sec. 4, the Simpson/trapezoid exponent)
+  The sign of the commutator term follows from Omega_2 = -1/2 int int [H(t1), H(t2)]
+  (Sec. 4, Eq. magnus); the paper's printed Simpson exponent carries the
+  opposite sign, which gives a second-order method (see the pins).
+* ``exact_slice_propagators`` -- U_j = exp(-i G_j) exactly (up to rounding),
+  by a Hermitian eigendecomposition G = Q diag(lam) Q^dagger, so
+  U_j = Q diag(exp(-i lam)) Q^dagger.  (Sec. 2.1 names decomposition methods as
+  the natural choice for Hermitian matrices; the CUDA path uses a series
+  instead, so the two agree only up to rounding.)
+* ``ordered_product``    -- U(T) = U_N ... U_1 (Sec. 2, Eq. slices: later slices
+  on the left) evaluated by the pairwise tree of Sec. 2.2: consecutive pairs
+  are multiplied, the number of matrices halves each round, an odd leftover
+  (the latest slice) is carried to the next round unchanged.
+* ``loss_and_gradient``  -- gate-fidelity loss L = 1 - |Tr(V^dagger U)|^2 / d^2 and
+  dL/dc_k(t_j) for the midpoint rule, with the Frechet derivative of exp taken
+  from the Daleckii-Krein formula (Sec. 7 motivates the gradient for GRAPE;
+  the paper itself gives no gradient formula).
+
+All arithmetic is complex128 / float64.  Parity is pinned by the tests in
+``tests/test_oracle_pins.py`` (closed forms, convergence orders, brute-force
+ODE integration, finite differences); no function here is "parity unpinned".
+"""
+
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+MIDPOINT = "midpoint"
+MAGNUS4_GL2 = "magnus4_gl2"
+MAGNUS4_SIMPSON = "magnus4_simpson"
+INTEGRATORS = (MIDPOINT, MAGNUS4_GL2, MAGNUS4_SIMPSON)
+
+
+def samples_per_run(n_steps: int, integrator: str) -> int:
+    """Number S of control samples per control for ``n_steps`` slices.
+
+    Midpoint: one sample per slice at its centre (S = N).  Gauss-Legendre:
+    two node samples per slice (S = 2N).  Simpson: both end points and the
+    centre of every slice, end points shared with the neighbours (S = 2N + 1).
+    """
+    if integrator == MIDPOINT:
+        return n_steps
+    if integrator == MAGNUS4_GL2:
+        return 2 * n_steps
+    if integrator == MAGNUS4_SIMPSON:
+        return 2 * n_steps + 1
+    raise ValueError(f"unknown integrator {integrator!r}")
+
+
+def hamiltonian(H0: np.ndarray, Hk: np.ndarray, c: np.ndarray) -> np.ndarray:
+    """H = H0 + sum_k c_k H_k  (Sec. 2, Eq. format_control).
+
+    ``H0`` is (d, d), ``Hk`` is (K, d, d), ``c`` is (K,) or (K, M) for M time
+    points; the result is (d, d) or (M, d, d).
+    """
+    H0 = np.asarray(H0, dtype=np.complex128)
+    Hk = np.asarray(Hk, dtype=np.complex128).reshape(-1, H0.shape[0], H0.shape[0])
+    c = np.asarray(c, dtype=np.float64)
+    if c.ndim == 1:
+        return H0 + np.einsum("k,kab->ab", c, Hk)
+    return H0[None] + np.einsum("km,kab->mab", c, Hk)
+
+
+def commutator(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    """[A, B] = AB - BA, batched over leading axes (Sec. 4)."""
+    return A @ B - B @ A
+
+
+def slice_exponents(H0, Hk, c, dt: float, integrator: str) -> np.ndarray:
+    """Hermitian exponents G_j (N, d, d) with U_j = exp(-i G_j).
+
+    ``c`` is the (K, S) array of real control samples, S as in
+    ``samples_per_run``; ``dt`` is the slice duration.
+    """
+    c = np.asarray(c, dtype=np.float64)
+    K = np.asarray(Hk).reshape(-1, np.asarray(H0).shape[0], np.asarray(H0).shape[0]).shape[0]
+    c = c.reshape(K, -1)
+    S = c.shape[1]
+    if integrator == MIDPOINT:
+        # Omega_1 by the mid-point rule: the Hamiltonian at the slice centre.
+        return dt * hamiltonian(H0, Hk, c)
+    if integrator == MAGNUS4_GL2:
+        if S % 2:
+            raise ValueError("Gauss-Legendre needs two samples per slice")
+        H1 = hamiltonian(H0, Hk, c[:, 0::2])  # node t_j + dt (1/2 - sqrt(3)/6)
+        H2 = hamiltonian(H0, Hk, c[:, 1::2])  # node t_j + dt (1/2 + sqrt(3)/6)
+        # Omega_1: two-node Gauss-Legendre quadrature of the Hamiltonian.
+        # Omega_2: the double integral of [H(t1), H(t2)] on the same nodes;
+        # Omega = -i G  gives the +i sign in front of [H1, H2].
+        return 0.5 * dt * (H1 + H2) + 1j * (math.sqrt(3.0) * dt * dt / 12.0) * commutator(H1, H2)
+    if integrator == MAGNUS4_SIMPSON:
+        if S % 2 != 1 or S < 1:
+            raise ValueError("Simpson needs 2N + 1 samples")
+        H1 = hamiltonian(H0, Hk, c[:, 0:S - 1:2])   # slice start
+        H2 = hamiltonian(H0, Hk, c[:, 1:S:2])       # slice centre
+        H3 = hamiltonian(H0, Hk, c[:, 2:S:2])       # slice end
+        # Omega_1 by Simpson's rule, Omega_2 by the trapezoidal rule (Sec. 4).
+        return (dt / 6.0) * (H1 + 4.0 * H2 + H3) + 1j * (dt * dt / 12.0) * commutator(H1, H3)
+    raise ValueError(f"unknown integrator {integrator!r}")
+
+
+def exact_slice_propagators(G: np.ndarray) -> np.ndarray:
+    """U_j = exp(-i G_j) for Hermitian G_j via eigendecomposition."""
+    G = np.asarray(G, dtype=np.complex128)
+    lam, Q = np.linalg.eigh(G)
+    return (Q * np.exp(-1j * lam)[..., None, :]) @ np.conj(np.swapaxes(Q, -1, -2))
+
+
+def ordered_product(U: np.ndarray) -> np.ndarray:
+    """U_N ... U_1 by the pairwise tree of Sec. 2.2.
+
+    ``U`` is (N, d, d) in time order (U[0] is the first slice).  Each round
+    multiplies consecutive pairs, the later slice on the left; an odd
+    leftover is carried to the next round unchanged.  N = 0 gives the
+    identity.
+    """
+    U = np.asarray(U, dtype=np.complex128)
+    if U.shape[0] == 0:
+        return np.eye(U.shape[-1], dtype=np.complex128)
+    while U.shape[0] > 1:
+        n = U.shape[0]
+        pairs = U[1:n - n % 2:2] @ U[0:n - n % 2:2]
+        U = np.concatenate([pairs, U[n - 1:]]) if n % 2 else pairs
+    return U[0]
+
+
+def propagate(H0, Hk, c, dt: float, integrator: str = MIDPOINT) -> np.ndarray:
+    """Full propagator U(T) = U_N ... U_1 (Sec. 2, Eq. slices)."""
+    G = slice_exponents(H0, Hk, c, dt, integrator)
+    return ordered_product(exact_slice_propagators(G))
+
+
+def gate_loss(U: np.ndarray, V: np.ndarray) -> float:
+    """L = 1 - |Tr(V^dagger U)|^2 / d^2 (gate infidelity)."""
+    d = U.shape[-1]
+    z = np.trace(np.conj(V).T @ U)
+    return float(1.0 - abs(z) ** 2 / d ** 2)
+
+
+def frechet_phi(lam: np.ndarray) -> np.ndarray:
+    """Divided differences of exp(-i x) on the eigenvalues (Daleckii-Krein).
+
+    Phi_ab = (e^{-i l_a} - e^{-i l_b}) / (-i l_a + i l_b), Phi_aa = e^{-i l_a},
+    written in the cancellation-free form
+    e^{-i (l_a + l_b)/2} * sin(delta) / delta with delta = (l_a - l_b)/2.
+    """
+    la = lam[..., :, None]
+    lb = lam[..., None, :]
+    delta = 0.5 * (la - lb)
+    return np.exp(-0.5j * (la + lb)) * np.sinc(delta / np.pi)
+
+
+def frechet_exp(G: np.ndarray, E: np.ndarray) -> np.ndarray:
+    """L_X(E): Frechet derivative of exp at X = -i G in direction E.
+
+    Daleckii-Krein: with G = Q diag(lam) Q^dagger,
+    L_X(E) = Q [ (Q^dagger E Q) o Phi ] Q^dagger  (o = elementwise product).
+    """
+    lam, Q = np.linalg.eigh(np.asarray(G, dtype=np.complex128))
+    Qh = np.conj(np.swapaxes(Q, -1, -2))
+    return Q @ ((Qh @ E @ Q) * frechet_phi(lam)) @ Qh
+
+
+def loss_and_gradient(H0, Hk, c, dt: float, V, integrator: str = MIDPOINT):
+    """Loss L, gradient dL/dc (K, N) and U(T) for the midpoint rule.
+
+    U = S_j U_j P_{j-1} with the exclusive prefix P_{j-1} = U_{j-1} ... U_1
+    and suffix S_j = U_N ... U_{j+1}; with z = Tr(V^dagger U),
+    dz/dc_kj = Tr(Lambda_j L_{X_j}(E_k)), Lambda_j = P_{j-1} V^dagger S_j,
+    X_j = -i G_j, E_k = dX_j/dc_kj = -i dt H_k, and
+    dL/dc_kj = -(2/d^2) Re(conj(z) dz/dc_kj).
+    """
+    if integrator != MIDPOINT:
+        raise NotImplementedError("the oracle gradient covers the midpoint rule")
+    H0 = np.asarray(H0, dtype=np.complex128)
+    d = H0.shape[0]
+    Hk = np.asarray(Hk, dtype=np.complex128).reshape(-1, d, d)
+    K = Hk.shape[0]
+    c = np.asarray(c, dtype=np.float64).reshape(K, -1)
+    N = c.shape[1]
+    V = np.asarray(V, dtype=np.complex128)
+
+    G = slice_exponents(H0, Hk, c, dt, MIDPOINT)
+    lam, Q = np.linalg.eigh(G)
+    Qh = np.conj(np.swapaxes(Q, -1, -2))
+    Uj = (Q * np.exp(-1j * lam)[:, None, :]) @ Qh
+
+    # exclusive prefixes P_{j-1} and suffixes S_j by their definitions
+    P = np.empty_like(Uj)
+    S = np.empty_like(Uj)
+    acc = np.eye(d, dtype=np.complex128)
+    for j in range(N):
+        P[j] = acc
+        acc = Uj[j] @ acc
+    U = acc
+    acc = np.eye(d, dtype=np.complex128)
+    for j in range(N - 1, -1, -1):
+        S[j] = acc
+        acc = acc @ Uj[j]
+
+    z = np.trace(np.conj(V).T @ U)
+    loss = float(1.0 - abs(z) ** 2 / d ** 2)
+    Lam = P @ np.conj(V).T @ S                       # (N, d, d)
+    E = -1j * dt * Hk                                # (K, d, d)
+    # Tr(Lam L_X(E)) = sum_ab (Q^dag Lam Q)_ba (Q^dag E Q)_ab Phi_ab
+    Lt = Qh @ Lam @ Q                                # (N, d, d)
+    Et = np.einsum("nab,kbc,ncd->nkad", Qh, E, Q)    # (N, K, d, d)
+    phi = frechet_phi(lam)                           # (N, d, d)
+    dz = np.einsum("nba,nkab,nab->kn", Lt, Et, phi)  # (K, N)
+    grad = -(2.0 / d ** 2) * np.real(np.conj(z) * dz)
+    return loss, grad, U
+
+
+def effective_control_count(n_ctrl: int) -> int:
+    """Number of effective controls of the fourth-order Magnus exponent.
+
+    The exponent is a real combination of H_k, i[H_0, H_k] and i[H_k, H_k']
+    for k < k': K + K + K(K-1)/2 = 3K/2 + K^2/2 (Sec. 4, Eq. magnus_coeffs).
+    """
+    return n_ctrl + n_ctrl + n_ctrl * (n_ctrl - 1) // 2
