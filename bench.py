@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark: time steps per second to the full propagator U(T) on one GB300.
+
+Workload (default): four coupled spin-1/2 (d = 16), eight controls, fourth-order
+Gauss-Legendre Magnus exponent, N = 2^20 slices, complex64 compute (the FP32
+path), timed next to the plain FP64 GPU path on the same inputs.  One
+"step" = one full propagation (every slice assembled, exponentiated and
+multiplied into U(T)) = one kernel launch.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  With --impl reference the FP64 CPU oracle is timed
+instead, on a bounded sample of the same workload, on the host cores.
+For N > 1 (torchrun) every rank propagates its own copy of the workload
+(independent replicas, weak scaling); the timed region is bracketed by
+barriers and the slowest rank's time counts.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time steps/sec to full U(T), by dim, vs plain FP64 GPU path at stated error"
+UNIT = "time steps/s"
+FP32_PEAK_TFLOPS_NOTE = "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz max SM clock"
+SM_COUNT, FP32_LANES, FP64_FMA_PER_SM_CLK = 152, 128, 2
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n-steps", type=int, default=1 << 20, help="slices of the workload")
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample", type=int, default=1 << 16, help="slices in the timed oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup(backend):
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend)
+    return rank, local, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- oracle (CPU baseline)
+
+_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import oracle
+from paper_2108_07126_gb300 import workloads as wl
+prob = wl.coupled_spins(n_steps={n})
+t0 = time.perf_counter()
+for _ in range({reps}):
+    U = oracle.propagate(prob.H0, prob.Hk, prob.c, prob.dt, prob.integrator)
+dt = time.perf_counter() - t0
+print(json.dumps({{"seconds": dt, "reps": {reps}, "n": {n}}}))
+"""
+
+
+def time_oracle(n_sample: int, reps: int = 1) -> dict:
+    """Time the FP64 oracle on the first n_sample slices, one thread, in a fresh process."""
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    code = _ORACLE_SNIPPET.format(root=ROOT, n=n_sample, reps=reps)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr)
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    return out
+
+
+def run_reference(args):
+    rank, _, world = dist_setup("gloo")
+    if rank != 0:
+        return
+    n = min(args.cpu_sample, 1 << 14)
+    per = []
+    for i in range(args.warmup + args.steps):
+        o = time_oracle(n)
+        if i >= args.warmup:
+            per.append(o["seconds"])
+    ms = 1e3 * statistics.mean(per)
+    value = n / (ms * 1e-3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(args.n_steps, "fp64"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {n} slices of the workload per step (FP64 eigendecomposition oracle)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def workload_config(n_steps, prec):
+    return {"workload": f"coupled_spins_d16_magnus4_gl2_N{n_steps}", "dim": 16, "n_steps": n_steps, "n_ctrl": 8,
+            "n_basis": 45, "integrator": "magnus4_gl2", "precision": prec,
+            "l2": f"flushed by a {L2_FLUSH_BYTES >> 20} MiB write between timed steps"}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+
+def flops_per_launch(st: dict) -> float:
+    """Algorithmic flops of one propagation: assembly + complex d x d products.
+
+    Assembly: 2 flops per (basis matrix, packed real entry): 2 * n_basis * d^2 per slice.
+    Each complex d x d product: 8 d^3 flops (Taylor/Paterson-Stockmeyer, squarings, tree).
+    """
+    d = st["dim"]
+    return 2.0 * st["n_basis"] * d * d * st["n_steps"] + 8.0 * d ** 3 * (st["exp_products"] + st["tree_products"])
+
+
+def time_launches(torch, fn, steps, warmup, flush):
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(steps):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, local, world = dist_setup("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2108_07126_gb300 import binding as b
+    from paper_2108_07126_gb300 import workloads as wl
+
+    prob = wl.coupled_spins(n_steps=args.n_steps)
+    N = prob.n_steps
+    prop = b.Propagator(local)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    # ---- FP32 path (headline)
+    H0 = torch.as_tensor(prob.H0).to(torch.complex64)
+    Hk = torch.as_tensor(prob.Hk).to(torch.complex64)
+    c32 = torch.as_tensor(prob.c).to(torch.float32).to(dev)
+    prop.set_hamiltonians(H0, Hk, prob.integrator)
+    prop.set_controls(c32, prob.dt, N)
+    U32 = torch.empty(16, 16, dtype=torch.complex64, device=dev)
+    fn32 = lambda: prop.propagate("fp32", out=U32)
+
+    gpu_uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    clocks = ClockSampler(gpu_uuid if gpu_uuid.startswith("GPU-") else f"GPU-{gpu_uuid}")
+    barrier(world)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    per32 = time_launches(torch, fn32, args.steps, args.warmup, flush)
+    torch.cuda.synchronize()
+    barrier(world)
+    t_wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    st32 = prop.stats()
+    ms32 = max_over_ranks(statistics.mean(per32), world, dev)
+    U32h = U32.cpu().numpy().astype(np.complex128)
+
+    # ---- plain FP64 GPU path on the same workload
+    prop.set_hamiltonians(torch.as_tensor(prob.H0), torch.as_tensor(prob.Hk), prob.integrator)
+    c64 = torch.as_tensor(prob.c).to(dev)
+    prop.set_controls(c64, prob.dt, N)
+    U64 = torch.empty(16, 16, dtype=torch.complex128, device=dev)
+    per64 = time_launches(torch, lambda: prop.propagate("fp64", out=U64), args.fp64_steps, 1, flush)
+    st64 = prop.stats()
+    ms64 = max_over_ranks(statistics.mean(per64), world, dev)
+    U64h = U64.cpu().numpy()
+    err32 = float(np.max(np.abs(U32h - U64h)))
+    unit_err = float(np.max(np.abs(U64h.conj().T @ U64h - np.eye(16))))
+
+    # ---- end to end through the C ABI with host buffers (pinned controls in, host U out)
+    c_host = torch.as_tensor(prob.c).to(torch.float32).pin_memory()
+    U_host = np.zeros((16, 16), np.complex64)
+    prop.set_hamiltonians(H0, Hk, prob.integrator)
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.parament_set_controls(prop.ctx, c_host.data_ptr(), b.PARAMENT_F32, N, prob.dt)
+        b.parament_propagate(prop.ctx, U_host.ctypes.data, b.PARAMENT_PREC_FP32)
+        t1 = time.perf_counter()
+        if i >= args.warmup:
+            e2e_times.append(t1 - t0)
+    e2e_s = max_over_ranks(statistics.mean(e2e_times), world, dev)
+    prop.close()
+
+    # ---- CPU baseline: the oracle on a bounded sample, rank 0 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        o = time_oracle(args.cpu_sample)
+        cpu = {"value": o["n"] / o["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {o['n']} slices of the workload, FP64 eigendecomposition oracle, one thread"}
+
+    if rank != 0:
+        return
+    fl32 = flops_per_launch(st32)
+    fl64 = flops_per_launch(st64)
+    peak32 = SM_COUNT * FP32_LANES * 2 * 2.07e9 / 1e12
+    peak64 = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * 2.07e9 / 1e12
+    ach32 = fl32 / (statistics.mean(per32) * 1e-3) / 1e12
+    ach64 = fl64 / (statistics.mean(per64) * 1e-3) / 1e12
+    value = world * N / (ms32 * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(workload_config(N, "fp32"), parallelism=("replicas" if world > 1 else "single")),
+        "fp64_gpu": {"value": world * N / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
+                     "steps": args.fp64_steps, "max_abs_err_vs_oracle_bound": 1e-11,
+                     "unitarity_err": unit_err, "exp_products": st64["exp_products"],
+                     "max_degree": st64["max_degree"], "max_squarings": st64["max_squarings"],
+                     "roofline": {"bound": "alu", "pipe": "fp64", "achieved": ach64, "peak": peak64,
+                                  "unit": "TFLOP/s", "frac": ach64 / peak64}},
+        "speedup_vs_fp64_gpu": ms64 / ms32,
+        "max_abs_err_vs_fp64_gpu": err32,
+        "kernel": {"grid_blocks": st32["grid_blocks"], "block_threads": st32["block_threads"],
+                   "leaves": st32["leaves"], "exp_products": st32["exp_products"],
+                   "tree_products": st32["tree_products"], "max_degree": st32["max_degree"],
+                   "max_squarings": st32["max_squarings"], "flops_per_launch": fl32},
+        "roofline": {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
+                     "traffic": None, "peak_note": FP32_PEAK_TFLOPS_NOTE},
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(c_host.numel() * 4),
+                "d2h_bytes_per_step": int(U_host.nbytes)},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+        "wall_s_timed": t_wall,
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,216 @@
+/*
+ * parament.h -- C ABI of the GB300 parallel-in-time propagator.
+ *
+ * Method (Herb & Welter, "Parallel time integration using Batched BLAS
+ * routines", arXiv 2108.07126): for H(t) = H0 + sum_k c_k(t) H_k (Sec. 2,
+ * Eq. format_control) the library forms, for every slice j of duration dt,
+ * the Hermitian exponent G_j (midpoint rule, Sec. 3.2; fourth-order Magnus
+ * exponent, Sec. 4), the slice propagator U_j = exp(-i G_j) (Sec. 2.1), and
+ * the ordered product U(T) = U_N ... U_1 (Sec. 2, Eq. slices) by a pairwise
+ * product tree (Sec. 2.2).  Usage follows the paper's state machine (Sec. 6,
+ * Fig. 5): create -> set_hamiltonians -> set_controls -> propagate (repeat)
+ * -> destroy.
+ *
+ * Conventions shared by every entry point:
+ *   - Every function returns a parament_status; nothing throws across the ABI.
+ *   - Complex matrices are dense, row-major, interleaved (re, im): the layout
+ *     of numpy/torch complex64 / complex128 arrays.
+ *   - A pointer argument may be host or device memory; the library asks the
+ *     CUDA runtime which one it is.  Device pointers are used in place, host
+ *     data is staged through buffers owned by the context.
+ *   - Work is enqueued on the context's stream.  A call that writes to host
+ *     memory waits for its own result; otherwise calls return without waiting.
+ *   - A context is neither thread-safe nor reentrant (Sec. 6): concurrent calls
+ *     on one context, or overlapping propagations of one context on several
+ *     streams, race on its workspace.  Distinct contexts are independent.
+ *   - Calling out of order returns PARAMENT_ERR_STATE and changes nothing.
+ */
+#ifndef PARAMENT_H
+#define PARAMENT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PARAMENT_VERSION_MAJOR 0
+#define PARAMENT_VERSION_MINOR 1
+
+typedef struct parament_ctx parament_ctx;
+
+typedef enum {
+    PARAMENT_OK = 0,
+    PARAMENT_ERR_INVALID_VALUE = 1, /* bad argument: null pointer, size out of range */
+    PARAMENT_ERR_STATE = 2,         /* call out of the create/set/propagate order */
+    PARAMENT_ERR_ALLOC = 3,         /* device or host allocation failed */
+    PARAMENT_ERR_CUDA = 4,          /* a CUDA runtime call failed (text in parament_last_error) */
+    PARAMENT_ERR_NONFINITE = 5,     /* NaN/Inf in Hamiltonians or controls */
+    PARAMENT_ERR_NOT_HERMITIAN = 6, /* H0 or some H_k is not Hermitian (tolerance: option) */
+    PARAMENT_ERR_TIMEOUT = 7,       /* a bounded device-side wait expired */
+    PARAMENT_ERR_UNSUPPORTED = 8    /* valid request this build does not implement */
+} parament_status;
+
+/* storage type of Hamiltonians and of the propagator U */
+typedef enum { PARAMENT_C64 = 0, PARAMENT_C128 = 1 } parament_dtype;
+/* storage type of the real control samples */
+typedef enum { PARAMENT_F32 = 0, PARAMENT_F64 = 1 } parament_real_dtype;
+
+/*
+ * Exponent of one slice t_j = j dt .. t_j + dt; S = number of samples per control.
+ *  MIDPOINT:          G_j = dt H(t_j + dt/2), one sample per slice, S = N
+ *                     (Sec. 3.2: G = H dt; Sec. 4: Omega_1 by the mid-point rule).
+ *  MAGNUS4_GL2:       G_j = dt/2 (H1 + H2) + i sqrt(3) dt^2 / 12 [H1, H2], H1, H2 sampled at
+ *                     t_j + dt (1/2 -+ sqrt(3)/6), S = 2N, samples interleaved per slice
+ *                     (Sec. 4, Eq. magnus: Omega_1 + Omega_2 on two Gauss-Legendre nodes).
+ *  MAGNUS4_SIMPSON:   G_j = dt/6 (H1 + 4 H2 + H3) + i dt^2 / 12 [H1, H3], samples at
+ *                     t_j, t_j + dt/2, t_j + dt shared between neighbours, S = 2N + 1
+ *                     (Sec. 4 and Eq. magnus_coeffs, commutator sign taken from Omega_2).
+ * The Magnus exponents are expanded into effective controls: the basis
+ * {H0, H_k, i[H0, H_k], i[H_k, H_k'] (k < k')}, 1 + K(K+3)/2 Hermitian matrices
+ * (Sec. 4, Eq. magnus_coeffs), built once by set_hamiltonians.
+ */
+typedef enum {
+    PARAMENT_MIDPOINT = 0,
+    PARAMENT_MAGNUS4_GL2 = 1,
+    PARAMENT_MAGNUS4_SIMPSON = 2
+} parament_integrator;
+
+/*
+ * Arithmetic of the exponential and of the product tree.
+ *  FP64: everything in double.
+ *  FP32: exponent assembly, exponential and the in-block tree in float; the
+ *        norm bound that picks the Taylor degree and the number of squarings,
+ *        and the product tree above the thread-block level, in double.
+ *  FP32_TC_*: FP32 with the complex products of d >= 32 on tensor cores
+ *        (split operands, FP32 accumulation).  Not implemented in this build:
+ *        PARAMENT_ERR_UNSUPPORTED.
+ */
+typedef enum {
+    PARAMENT_PREC_FP64 = 0,
+    PARAMENT_PREC_FP32 = 1,
+    PARAMENT_PREC_FP32_TC_BF16X3 = 2,
+    PARAMENT_PREC_FP32_TC_TF32X3 = 3
+} parament_precision;
+
+/* keys of parament_set_option / parament_get_option */
+typedef enum {
+    /* 0 (default) = choose the Taylor degree per slice from the norm bound;
+       m > 0 = force degree m (one of 1, 2, 4, 6, 9, 12), squarings still from the bound */
+    PARAMENT_OPT_TAYLOR_DEGREE = 1,
+    /* thread blocks of the fused kernel; 0 (default) = fill every SM */
+    PARAMENT_OPT_GRID_BLOCKS = 2,
+    /* warps per thread block; 0 (default) = largest that fits shared memory, capped at 8 */
+    PARAMENT_OPT_BLOCK_WARPS = 3,
+    /* 1 (default) = reject non-Hermitian H in set_hamiltonians; 0 = skip the check */
+    PARAMENT_OPT_CHECK_HERMITIAN = 4,
+    /* extra squarings added to every slice (default 0; accuracy experiments) */
+    PARAMENT_OPT_EXTRA_SQUARINGS = 5,
+    /* Hermiticity tolerance in units of 1e-12 relative to max |H_ab| (default 1000, i.e. 1e-9) */
+    PARAMENT_OPT_HERMITIAN_TOL_E12 = 7
+} parament_option;
+
+/* per-call diagnostics of the most recent propagate (see parament_get_stats) */
+typedef struct {
+    int64_t n_steps;          /* slices propagated */
+    int32_t dim;              /* d */
+    int32_t n_basis;          /* 1 + number of (effective) controls */
+    int32_t grid_blocks;      /* thread blocks launched */
+    int32_t block_threads;    /* threads per block */
+    int32_t leaves;           /* sequential leaf products below the pairwise tree */
+    int32_t max_degree;       /* largest Taylor degree used */
+    int32_t max_squarings;    /* largest number of squarings used */
+    int32_t reserved0;
+    int64_t exp_products;     /* complex d x d products in exponentials and squarings */
+    int64_t tree_products;    /* complex d x d products in the product tree */
+    uint32_t device_status;   /* PARAMENT_DEV_* bits raised by the kernels */
+    uint32_t reserved1;
+    double kernel_ms;         /* device time of the propagation kernels (events) */
+} parament_stats;
+
+#define PARAMENT_DEV_NONFINITE_NORM 0x1u /* a slice's norm bound was NaN/Inf */
+#define PARAMENT_DEV_NORM_CAPPED 0x2u    /* a norm exceeded the largest scaling in the table */
+
+/* Library version as major * 1000 + minor. */
+int parament_version(void);
+
+/*
+ * Create a context on CUDA device `device`, enqueuing on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * handle, owned by the caller, released by parament_destroy.  Sec. 6: the
+ * context stores the integrator state.
+ */
+int parament_create(parament_ctx **out, int device, void *cuda_stream);
+
+/* Release a context and every device buffer it owns; NULL is a no-op.
+   Waits for the context's stream.  Sec. 6 (Parament_free). */
+int parament_destroy(parament_ctx *ctx);
+
+/* Switch the stream later calls enqueue on (NULL = legacy default stream). */
+int parament_set_stream(parament_ctx *ctx, void *cuda_stream);
+
+/*
+ * Upload H0 (d x d) and the K control Hamiltonians Hk (K x d x d, contiguous)
+ * and choose the integrator (Sec. 6, Parament_setHamiltonian; the Magnus
+ * choice makes the library form the commutator basis here, Sec. 4).
+ * `dtype` is the storage type of H0/Hk and of every later U_out.  The data are
+ * copied; the caller keeps ownership.  d in [1, 16] for this build
+ * (PARAMENT_ERR_UNSUPPORTED above), 0 <= K <= 16.  Hk may be NULL when K = 0.
+ * Resets any controls set before.  Errors: INVALID_VALUE, NONFINITE,
+ * NOT_HERMITIAN (checked on the device; the call waits for the check).
+ */
+int parament_set_hamiltonians(parament_ctx *ctx, int dim, int n_ctrl, const void *H0, const void *Hk,
+                              parament_dtype dtype, parament_integrator integrator);
+
+/*
+ * Set the control samples c (K x S, row-major, c[k * S + s]) for n_steps
+ * slices of duration dt (Sec. 3.2: amplitudes sampled at equidistant times;
+ * S per integrator as documented above).  A device pointer is borrowed, not
+ * copied: it must stay valid and unchanged until the propagations that use
+ * it have run on the stream.  Host data is copied into a context buffer.
+ * 0 <= n_steps < 2^31 (0 gives U = I), dt finite.  Requires set_hamiltonians.
+ */
+int parament_set_controls(parament_ctx *ctx, const void *c, parament_real_dtype cdtype, int64_t n_steps,
+                          double dt);
+
+/*
+ * Compute U(T) = U_N ... U_1 into U_out (d x d, the dtype of
+ * set_hamiltonians) with arithmetic `prec` (Sec. 2, Eq. slices; Sec. 2.2).
+ * One kernel launch: per slice it forms G_j from the control samples, bounds
+ * ||G_j||_1 in FP64 from the coefficients (Sec. 3.2's triangle-inequality
+ * bound, per slice), evaluates a Taylor polynomial of exp(-i G_j / 2^s)
+ * (Paterson-Stockmeyer) and squares s times, multiplies consecutive slices in
+ * sequential leaves, then combines the leaves pairwise in shared memory and
+ * the blocks' partial products pairwise through global memory.
+ * Requires set_hamiltonians and set_controls.
+ */
+int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec);
+
+/* Diagnostics of the latest propagate; waits for the stream. */
+int parament_get_stats(parament_ctx *ctx, parament_stats *out);
+
+/* Set / read a numerics or launch option (parament_option).  Sec. 6 mentions
+   helper functions that tweak the numerics, e.g. the series degree. */
+int parament_set_option(parament_ctx *ctx, int key, int64_t value);
+int parament_get_option(const parament_ctx *ctx, int key, int64_t *value);
+
+/*
+ * Taylor threshold theta_m for unit roundoff `u`: the largest x with
+ * x^(m+1)/(m+1)! * e^x <= u, the truncation bound of the degree-m Taylor
+ * polynomial of exp(A) for ||A|| <= x.  Host-only helper (no GPU needed);
+ * returns a negative value for m < 1.
+ */
+double parament_taylor_theta(int m, double u);
+
+/* Static text for a status code. */
+const char *parament_status_string(int status);
+
+/* Text of the last error on this context (empty if none); valid until the next call. */
+const char *parament_last_error(const parament_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PARAMENT_H */

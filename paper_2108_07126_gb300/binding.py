@@ -1,0 +1,273 @@
+"""Thin ctypes binding of libparament.so (include/parament.h).
+
+The functions keep the C names and take the same arguments (device or host
+pointers as Python ints); they only marshal arguments and turn a non-zero
+status into ``ParamentError``.  Every step of the propagation runs in the CUDA
+library.  Importing this module fails loudly if the library has not been
+built -- there is no CPU fallback.
+
+``Propagator`` wraps one context for torch tensors: it passes ``data_ptr()``
+values and the current torch CUDA stream.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libparament.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build it with `python -m paper_2108_07126_gb300.build` "
+        "(the propagator has no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# ---- enums (parament.h)
+PARAMENT_OK = 0
+PARAMENT_ERR_INVALID_VALUE = 1
+PARAMENT_ERR_STATE = 2
+PARAMENT_ERR_ALLOC = 3
+PARAMENT_ERR_CUDA = 4
+PARAMENT_ERR_NONFINITE = 5
+PARAMENT_ERR_NOT_HERMITIAN = 6
+PARAMENT_ERR_TIMEOUT = 7
+PARAMENT_ERR_UNSUPPORTED = 8
+
+PARAMENT_C64 = 0
+PARAMENT_C128 = 1
+PARAMENT_F32 = 0
+PARAMENT_F64 = 1
+
+PARAMENT_MIDPOINT = 0
+PARAMENT_MAGNUS4_GL2 = 1
+PARAMENT_MAGNUS4_SIMPSON = 2
+
+PARAMENT_PREC_FP64 = 0
+PARAMENT_PREC_FP32 = 1
+PARAMENT_PREC_FP32_TC_BF16X3 = 2
+PARAMENT_PREC_FP32_TC_TF32X3 = 3
+
+PARAMENT_OPT_TAYLOR_DEGREE = 1
+PARAMENT_OPT_GRID_BLOCKS = 2
+PARAMENT_OPT_BLOCK_WARPS = 3
+PARAMENT_OPT_CHECK_HERMITIAN = 4
+PARAMENT_OPT_EXTRA_SQUARINGS = 5
+PARAMENT_OPT_HERMITIAN_TOL_E12 = 7
+
+PARAMENT_DEV_NONFINITE_NORM = 0x1
+PARAMENT_DEV_NORM_CAPPED = 0x2
+
+INTEGRATORS = {"midpoint": PARAMENT_MIDPOINT, "magnus4_gl2": PARAMENT_MAGNUS4_GL2,
+               "magnus4_simpson": PARAMENT_MAGNUS4_SIMPSON}
+PRECISIONS = {"fp64": PARAMENT_PREC_FP64, "fp32": PARAMENT_PREC_FP32,
+              "fp32_tc_bf16x3": PARAMENT_PREC_FP32_TC_BF16X3, "fp32_tc_tf32x3": PARAMENT_PREC_FP32_TC_TF32X3}
+
+
+class parament_stats(ctypes.Structure):
+    _fields_ = [
+        ("n_steps", ctypes.c_int64),
+        ("dim", ctypes.c_int32),
+        ("n_basis", ctypes.c_int32),
+        ("grid_blocks", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
+        ("leaves", ctypes.c_int32),
+        ("max_degree", ctypes.c_int32),
+        ("max_squarings", ctypes.c_int32),
+        ("reserved0", ctypes.c_int32),
+        ("exp_products", ctypes.c_int64),
+        ("tree_products", ctypes.c_int64),
+        ("device_status", ctypes.c_uint32),
+        ("reserved1", ctypes.c_uint32),
+        ("kernel_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_ if not name.startswith("reserved")}
+
+
+_vp = ctypes.c_void_p
+_SIGS = {
+    "parament_version": ([], ctypes.c_int),
+    "parament_create": ([ctypes.POINTER(_vp), ctypes.c_int, _vp], ctypes.c_int),
+    "parament_destroy": ([_vp], ctypes.c_int),
+    "parament_set_stream": ([_vp, _vp], ctypes.c_int),
+    "parament_set_hamiltonians": ([_vp, ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int],
+                                  ctypes.c_int),
+    "parament_set_controls": ([_vp, _vp, ctypes.c_int, ctypes.c_int64, ctypes.c_double], ctypes.c_int),
+    "parament_propagate": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
+    "parament_get_stats": ([_vp, ctypes.POINTER(parament_stats)], ctypes.c_int),
+    "parament_set_option": ([_vp, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
+    "parament_get_option": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "parament_taylor_theta": ([ctypes.c_int, ctypes.c_double], ctypes.c_double),
+    "parament_status_string": ([ctypes.c_int], ctypes.c_char_p),
+    "parament_last_error": ([_vp], ctypes.c_char_p),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+
+
+class ParamentError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{parament_status_string(status)}: {message}")
+        self.status = status
+
+
+def _check(status: int, ctx=None) -> None:
+    if status != PARAMENT_OK:
+        raise ParamentError(status, parament_last_error(ctx) if ctx else "")
+
+
+# ---- C-named wrappers -------------------------------------------------------------------
+
+def parament_version() -> int:
+    return _lib.parament_version()
+
+
+def parament_status_string(status: int) -> str:
+    return _lib.parament_status_string(int(status)).decode()
+
+
+def parament_last_error(ctx) -> str:
+    return _lib.parament_last_error(ctx).decode()
+
+
+def parament_create(device: int = 0, stream: int | None = None):
+    h = _vp()
+    _check(_lib.parament_create(ctypes.byref(h), int(device), stream or None))
+    return h
+
+
+def parament_destroy(ctx) -> None:
+    _check(_lib.parament_destroy(ctx))
+
+
+def parament_set_stream(ctx, stream: int | None) -> None:
+    _check(_lib.parament_set_stream(ctx, stream or None), ctx)
+
+
+def parament_set_hamiltonians(ctx, dim: int, n_ctrl: int, H0_ptr: int, Hk_ptr: int | None, dtype: int,
+                              integrator: int) -> None:
+    _check(_lib.parament_set_hamiltonians(ctx, int(dim), int(n_ctrl), H0_ptr, Hk_ptr or None, int(dtype),
+                                          int(integrator)), ctx)
+
+
+def parament_set_controls(ctx, c_ptr: int | None, cdtype: int, n_steps: int, dt: float) -> None:
+    _check(_lib.parament_set_controls(ctx, c_ptr or None, int(cdtype), int(n_steps), float(dt)), ctx)
+
+
+def parament_propagate(ctx, U_ptr: int, prec: int) -> None:
+    _check(_lib.parament_propagate(ctx, U_ptr, int(prec)), ctx)
+
+
+def parament_get_stats(ctx) -> dict:
+    s = parament_stats()
+    _check(_lib.parament_get_stats(ctx, ctypes.byref(s)), ctx)
+    return s.as_dict()
+
+
+def parament_set_option(ctx, key: int, value: int) -> None:
+    _check(_lib.parament_set_option(ctx, int(key), int(value)), ctx)
+
+
+def parament_get_option(ctx, key: int) -> int:
+    v = ctypes.c_int64()
+    _check(_lib.parament_get_option(ctx, int(key), ctypes.byref(v)), ctx)
+    return v.value
+
+
+def parament_taylor_theta(m: int, u: float) -> float:
+    return _lib.parament_taylor_theta(int(m), float(u))
+
+
+def raw_call(name: str, *args) -> int:
+    """Call a C entry point directly and return its status (for tests of the error paths)."""
+    return getattr(_lib, name)(*args)
+
+
+# ---- torch convenience wrapper ------------------------------------------------------------
+
+class Propagator:
+    """One library context bound to a CUDA device and the current torch stream.
+
+    ``set_hamiltonians(H0, Hk, integrator)`` takes complex64/complex128 tensors or
+    arrays; ``set_controls(c, dt)`` a real (K, S) tensor; ``propagate(prec)``
+    returns U(T) as a device tensor of the Hamiltonians' dtype.
+    """
+
+    def __init__(self, device: int = 0):
+        import torch
+
+        self._torch = torch
+        self.device = torch.device("cuda", device)
+        self.ctx = parament_create(device, torch.cuda.current_stream(self.device).cuda_stream)
+        self._keep = []
+        self.dim = None
+        self.cdtype = None
+
+    def close(self):
+        if self.ctx is not None:
+            parament_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _sync_stream(self):
+        parament_set_stream(self.ctx, self._torch.cuda.current_stream(self.device).cuda_stream)
+
+    def set_option(self, key: int, value: int):
+        parament_set_option(self.ctx, key, value)
+
+    def set_hamiltonians(self, H0, Hk, integrator: str = "midpoint"):
+        torch = self._torch
+        H0 = torch.as_tensor(H0)
+        if H0.dtype not in (torch.complex64, torch.complex128):
+            H0 = H0.to(torch.complex128)
+        d = H0.shape[-1]
+        Hk = torch.as_tensor(Hk).to(H0.dtype).reshape(-1, d, d) if Hk is not None else torch.zeros(0, d, d,
+                                                                                               dtype=H0.dtype)
+        H0 = H0.to(self.device).contiguous()
+        Hk = Hk.to(self.device).contiguous()
+        self._sync_stream()
+        parament_set_hamiltonians(self.ctx, d, Hk.shape[0], H0.data_ptr(), Hk.data_ptr() if Hk.numel() else None,
+                                  PARAMENT_C128 if H0.dtype == torch.complex128 else PARAMENT_C64,
+                                  INTEGRATORS[integrator])
+        self.dim = d
+        self.dtype = H0.dtype
+        self.n_ctrl = Hk.shape[0]
+        self.integrator = integrator
+        self._keep = [H0, Hk]
+
+    def set_controls(self, c, dt: float, n_steps: int | None = None):
+        torch = self._torch
+        c = torch.as_tensor(c)
+        if c.dtype not in (torch.float32, torch.float64):
+            c = c.to(torch.float64)
+        c = c.to(self.device).contiguous()
+        if n_steps is None:
+            S = c.shape[-1] if c.numel() else 0
+            n_steps = {"midpoint": S, "magnus4_gl2": S // 2, "magnus4_simpson": max(S - 1, 0) // 2}[self.integrator]
+        self._sync_stream()
+        parament_set_controls(self.ctx, c.data_ptr() if c.numel() else None,
+                              PARAMENT_F64 if c.dtype == torch.float64 else PARAMENT_F32, n_steps, dt)
+        self._ctrl = c
+        self.n_steps = n_steps
+
+    def propagate(self, prec: str = "fp64", out=None):
+        torch = self._torch
+        if out is None:
+            out = torch.empty(self.dim, self.dim, dtype=self.dtype, device=self.device)
+        self._sync_stream()
+        parament_propagate(self.ctx, out.data_ptr(), PRECISIONS[prec])
+        return out
+
+    def stats(self) -> dict:
+        return parament_get_stats(self.ctx)

@@ -1,0 +1,727 @@
+// Host side of the C ABI declared in include/parament.h, plus the set-up
+// kernels (basis construction, Hermiticity check, control conversion).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/parament.h"
+#include "pm_common.cuh"
+
+namespace pm {
+#define PM_DECL_D(D)                                                                                     \
+    cudaError_t fused_dispatch_d##D(int, int, const FusedParams &, int, int, size_t, cudaStream_t);      \
+    int fused_blocks_per_sm_d##D(int, int, int, size_t);                                                 \
+    size_t fused_smem_d##D(int, int, int);                                                               \
+    int fused_groups_per_warp_d##D();
+PM_DECL_D(2)
+PM_DECL_D(4)
+PM_DECL_D(8)
+PM_DECL_D(16)
+#undef PM_DECL_D
+}  // namespace pm
+
+using namespace pm;
+
+namespace {
+
+constexpr int kMaxDim = 16;
+constexpr int kLeafMinSteps = 8;  // fewer blocks for short runs: each leaf gets >= 8 slices
+
+struct Workspace {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct parament_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int state = 0;  // 0 created, 1 Hamiltonians set, 2 controls set
+    int sm_count = 0;
+    size_t smem_optin = 0;
+    int max_grid = 0;
+
+    int dim = 0, dpad = 0, K = 0, nb = 0;
+    parament_dtype dtype = PARAMENT_C128;
+    parament_integrator integ = PARAMENT_MIDPOINT;
+
+    Workspace hraw, full, packed64, packed32, bnorm, partials, tickets, counters, status, check;
+    Workspace ctrl_copy, ctrl_conv, uout;
+
+    const void *ctrl = nullptr;
+    parament_real_dtype cdtype = PARAMENT_F64;
+    int64_t n_steps = 0, S = 0;
+    double dt = 0.0;
+
+    int64_t opt_degree = 0, opt_grid = 0, opt_warps = 0, opt_check_herm = 1, opt_extra_sq = 0, opt_herm_tol = 1000;
+
+    parament_stats last{};
+    std::string err;
+};
+
+namespace {
+
+int set_err(parament_ctx *ctx, int status, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return status;
+}
+
+#define PM_CUDA(call)                                                                                    \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) {                                                                         \
+            cudaGetLastError();                                                                          \
+            return set_err(ctx, PARAMENT_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));    \
+        }                                                                                                \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int ws_reserve(parament_ctx *ctx, Workspace &w, size_t bytes) {
+    if (w.bytes >= bytes && w.ptr) return PARAMENT_OK;
+    if (w.ptr) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(w.ptr);
+        w.ptr = nullptr;
+        w.bytes = 0;
+    }
+    if (bytes == 0) return PARAMENT_OK;
+    cudaError_t e = cudaMalloc(&w.ptr, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        w.ptr = nullptr;
+        return set_err(ctx, PARAMENT_ERR_ALLOC, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    w.bytes = bytes;
+    return PARAMENT_OK;
+}
+
+void ws_free(Workspace &w) {
+    if (w.ptr) cudaFree(w.ptr);
+    w.ptr = nullptr;
+    w.bytes = 0;
+}
+
+bool is_device_ptr(const void *p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int pad_dim(int d) {
+    if (d <= 2) return 2;
+    if (d <= 4) return 4;
+    if (d <= 8) return 8;
+    return 16;
+}
+
+int n_basis_for(int K, parament_integrator integ) {
+    return integ == PARAMENT_MIDPOINT ? 1 + K : 1 + 2 * K + K * (K - 1) / 2;
+}
+
+int64_t samples_for(int64_t n, parament_integrator integ) {
+    switch (integ) {
+        case PARAMENT_MIDPOINT: return n;
+        case PARAMENT_MAGNUS4_GL2: return 2 * n;
+        case PARAMENT_MAGNUS4_SIMPSON: return 2 * n + 1;
+    }
+    return n;
+}
+
+// ------------------------------------------------------------------ set-up kernels
+
+// order-preserving bit pattern of a non-negative double, for atomicMax
+__device__ inline unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+template <typename InT>
+__global__ void check_hermitian_kernel(const InT *raw, int d, int n_mat, unsigned long long *out /*[3]*/) {
+    const int m = blockIdx.x;
+    double err = 0.0, mx = 0.0;
+    int bad = 0;
+    for (int t = threadIdx.x; t < d * d; t += blockDim.x) {
+        const int i = t / d, j = t % d;
+        const InT a = raw[(size_t)m * d * d + i * d + j];
+        const InT b = raw[(size_t)m * d * d + j * d + i];
+        const double ax = a.x, ay = a.y, bx = b.x, by = b.y;
+        if (!isfinite(ax) || !isfinite(ay)) bad = 1;
+        err = fmax(err, hypot(ax - bx, ay + by));
+        mx = fmax(mx, hypot(ax, ay));
+    }
+    if (bad) atomicOr(&out[2], 1ull);
+    if (isfinite(err)) atomicMax(&out[0], dbits(err));
+    if (isfinite(mx)) atomicMax(&out[1], dbits(mx));
+}
+
+// Basis B_e (FP64, padded to Dp): H0, H_k and, for the Magnus exponents,
+// i[H0, H_k] and i[H_a, H_b] (a < b), the effective control Hamiltonians of
+// Sec. 4, Eq. magnus_coeffs.
+template <typename InT>
+__global__ void build_basis_kernel(const InT *raw, int d, int Dp, int K, int magnus, double2 *full) {
+    const int e = blockIdx.x;
+    int a = -1, b = -1, src = -1;
+    if (e < 1 + K) {
+        src = e;
+    } else if (e < 1 + 2 * K) {
+        a = 0;
+        b = e - K;  // raw index of H_k is k + 1
+    } else {
+        int pidx = e - (1 + 2 * K);
+        for (int x = 0; x < K && a < 0; ++x) {
+            const int cnt = K - 1 - x;
+            if (pidx < cnt) { a = 1 + x; b = 1 + x + 1 + pidx; }
+            else pidx -= cnt;
+        }
+    }
+    (void)magnus;
+    for (int t = threadIdx.x; t < Dp * Dp; t += blockDim.x) {
+        const int i = t / Dp, j = t % Dp;
+        double2 v = make_double2(0.0, 0.0);
+        if (i < d && j < d) {
+            if (src >= 0) {
+                const InT x = raw[(size_t)src * d * d + i * d + j];
+                v = make_double2((double)x.x, (double)x.y);
+            } else {
+                const InT *A = raw + (size_t)a * d * d;
+                const InT *B = raw + (size_t)b * d * d;
+                double re = 0.0, im = 0.0;  // [A, B]_ij
+                for (int l = 0; l < d; ++l) {
+                    const double2 ail = make_double2(A[i * d + l].x, A[i * d + l].y);
+                    const double2 blj = make_double2(B[l * d + j].x, B[l * d + j].y);
+                    const double2 bil = make_double2(B[i * d + l].x, B[i * d + l].y);
+                    const double2 alj = make_double2(A[l * d + j].x, A[l * d + j].y);
+                    re += ail.x * blj.x - ail.y * blj.y - (bil.x * alj.x - bil.y * alj.y);
+                    im += ail.x * blj.y + ail.y * blj.x - (bil.x * alj.y + bil.y * alj.x);
+                }
+                v = make_double2(-im, re);  // i * [A, B]
+            }
+        }
+        full[(size_t)e * Dp * Dp + t] = v;
+    }
+}
+
+// Packed real form of each Hermitian basis matrix (upper triangle: real parts,
+// strictly lower triangle: imaginary parts) and its FP64 1-norm.
+__global__ void pack_basis_kernel(const double2 *full, int Dp, double *p64, float *p32, double *bnorm) {
+    const int e = blockIdx.x;
+    const double2 *B = full + (size_t)e * Dp * Dp;
+    for (int t = threadIdx.x; t < Dp * Dp; t += blockDim.x) {
+        const int i = t / Dp, j = t % Dp;
+        const double2 v = B[t];
+        const double x = (i <= j) ? v.x : v.y;
+        p64[(size_t)e * Dp * Dp + t] = x;
+        p32[(size_t)e * Dp * Dp + t] = (float)x;
+    }
+    __shared__ double colsum[kMaxDim];
+    if (threadIdx.x < Dp) {
+        double s = 0.0;
+        for (int i = 0; i < Dp; ++i) s += hypot(B[i * Dp + threadIdx.x].x, B[i * Dp + threadIdx.x].y);
+        colsum[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int j = 0; j < Dp; ++j) m = fmax(m, colsum[j]);
+        // the packed FP32 basis is a rounded copy: widen the bound by its relative rounding
+        bnorm[e] = m * (1.0 + 4.0 * 5.960464477539063e-08 * Dp);
+    }
+}
+
+template <typename From, typename To>
+__global__ void convert_kernel(const From *src, To *dst, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (To)src[i];
+}
+
+// ------------------------------------------------------------------ Taylor classes
+
+struct Cand {
+    double cap;
+    int cost, m, q, r, s;
+};
+
+const int kDegrees[][3] = {{1, 1, 1}, {2, 2, 1}, {4, 2, 2}, {6, 3, 2}, {9, 3, 3}, {12, 3, 4}};  // m, q, r
+
+int build_classes(double u, int force_m, FusedParams &p) {
+    std::vector<Cand> all;
+    for (int s = 0; s <= 62; ++s) {
+        for (const auto &dg : kDegrees) {
+            const int m = dg[0], q = dg[1], r = dg[2];
+            if (force_m > 0 && m != force_m) continue;
+            const double th = parament_taylor_theta(m, u);
+            all.push_back({std::ldexp(th, s), (q - 1) + (r - 1) + s, m, q, r, s});
+        }
+    }
+    if (all.empty()) return 0;
+    std::sort(all.begin(), all.end(), [](const Cand &a, const Cand &b) {
+        return a.cap != b.cap ? a.cap > b.cap : a.cost < b.cost;
+    });
+    std::vector<Cand> keep;
+    int best = 1 << 30;
+    for (const auto &c : all)
+        if (c.cost < best) {
+            keep.push_back(c);
+            best = c.cost;
+        }
+    std::reverse(keep.begin(), keep.end());
+    if ((int)keep.size() > kMaxClasses) keep.resize(kMaxClasses);
+    p.n_cls = (int)keep.size();
+    for (int i = 0; i < p.n_cls; ++i) {
+        p.cls_cap[i] = keep[i].cap;
+        p.cls_code[i] = cls_pack(keep[i].m, keep[i].q, keep[i].r, keep[i].s);
+    }
+    double f = 1.0;
+    for (int k = 0; k <= kMaxDegree; ++k) {
+        if (k > 0) f /= k;
+        p.coef_d[k] = f;
+        p.coef_f[k] = (float)f;
+    }
+    return p.n_cls;
+}
+
+cudaError_t fused_dispatch(int Dp, int fp64, int integ, const FusedParams &p, int grid, int warps, size_t smem,
+                           cudaStream_t st) {
+    switch (Dp) {
+        case 2: return fused_dispatch_d2(fp64, integ, p, grid, warps, smem, st);
+        case 4: return fused_dispatch_d4(fp64, integ, p, grid, warps, smem, st);
+        case 8: return fused_dispatch_d8(fp64, integ, p, grid, warps, smem, st);
+        case 16: return fused_dispatch_d16(fp64, integ, p, grid, warps, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+int fused_blocks_per_sm(int Dp, int fp64, int integ, int warps, size_t smem) {
+    switch (Dp) {
+        case 2: return fused_blocks_per_sm_d2(fp64, integ, warps, smem);
+        case 4: return fused_blocks_per_sm_d4(fp64, integ, warps, smem);
+        case 8: return fused_blocks_per_sm_d8(fp64, integ, warps, smem);
+        case 16: return fused_blocks_per_sm_d16(fp64, integ, warps, smem);
+    }
+    return 0;
+}
+size_t fused_smem(int Dp, int fp64, int nb, int warps) {
+    switch (Dp) {
+        case 2: return fused_smem_d2(fp64, nb, warps);
+        case 4: return fused_smem_d4(fp64, nb, warps);
+        case 8: return fused_smem_d8(fp64, nb, warps);
+        case 16: return fused_smem_d16(fp64, nb, warps);
+    }
+    return 0;
+}
+int fused_gpw(int Dp) {
+    switch (Dp) {
+        case 2: return fused_groups_per_warp_d2();
+        case 4: return fused_groups_per_warp_d4();
+        case 8: return fused_groups_per_warp_d8();
+        case 16: return fused_groups_per_warp_d16();
+    }
+    return 1;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+int parament_version(void) { return PARAMENT_VERSION_MAJOR * 1000 + PARAMENT_VERSION_MINOR; }
+
+const char *parament_status_string(int status) {
+    switch (status) {
+        case PARAMENT_OK: return "PARAMENT_OK";
+        case PARAMENT_ERR_INVALID_VALUE: return "PARAMENT_ERR_INVALID_VALUE";
+        case PARAMENT_ERR_STATE: return "PARAMENT_ERR_STATE";
+        case PARAMENT_ERR_ALLOC: return "PARAMENT_ERR_ALLOC";
+        case PARAMENT_ERR_CUDA: return "PARAMENT_ERR_CUDA";
+        case PARAMENT_ERR_NONFINITE: return "PARAMENT_ERR_NONFINITE";
+        case PARAMENT_ERR_NOT_HERMITIAN: return "PARAMENT_ERR_NOT_HERMITIAN";
+        case PARAMENT_ERR_TIMEOUT: return "PARAMENT_ERR_TIMEOUT";
+        case PARAMENT_ERR_UNSUPPORTED: return "PARAMENT_ERR_UNSUPPORTED";
+    }
+    return "PARAMENT_UNKNOWN_STATUS";
+}
+
+const char *parament_last_error(const parament_ctx *ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+double parament_taylor_theta(int m, double u) {
+    if (m < 1 || !(u > 0.0) || !(u < 1.0)) return -1.0;
+    // g(x) = (m+1) ln x - ln (m+1)! + x - ln u is increasing for x > 0
+    const double lf = std::lgamma((double)m + 2.0), lu = std::log(u);
+    auto g = [&](double x) { return (m + 1) * std::log(x) - lf + x - lu; };
+    double lo = 0.0, hi = 1.0;
+    for (int i = 0; i < 64 && g(hi) < 0.0; ++i) hi *= 2.0;
+    for (int i = 0; i < 200; ++i) {
+        const double mid = 0.5 * (lo + hi);
+        if (g(mid) <= 0.0) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+int parament_create(parament_ctx **out, int device, void *cuda_stream) {
+    if (!out) return PARAMENT_ERR_INVALID_VALUE;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return PARAMENT_ERR_CUDA;
+    }
+    if (device < 0 || device >= ndev) return PARAMENT_ERR_INVALID_VALUE;
+    parament_ctx *ctx = new (std::nothrow) parament_ctx();
+    if (!ctx) return PARAMENT_ERR_ALLOC;
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    DeviceGuard guard(device);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        cudaGetLastError();
+        delete ctx;
+        return PARAMENT_ERR_CUDA;
+    }
+    ctx->sm_count = prop.multiProcessorCount;
+    ctx->smem_optin = prop.sharedMemPerBlockOptin;
+    ctx->max_grid = prop.multiProcessorCount * 8;
+    int st = ws_reserve(ctx, ctx->counters, 8 * sizeof(unsigned long long));
+    if (st == PARAMENT_OK) st = ws_reserve(ctx, ctx->status, 2 * sizeof(unsigned));
+    if (st == PARAMENT_OK) st = ws_reserve(ctx, ctx->tickets, 2 * (size_t)ctx->max_grid * sizeof(unsigned));
+    if (st == PARAMENT_OK) st = ws_reserve(ctx, ctx->check, 4 * sizeof(unsigned long long));
+    if (st != PARAMENT_OK) {
+        parament_destroy(ctx);
+        return st;
+    }
+    if (cudaMemset(ctx->counters.ptr, 0, ctx->counters.bytes) != cudaSuccess ||
+        cudaMemset(ctx->status.ptr, 0, ctx->status.bytes) != cudaSuccess ||
+        cudaMemset(ctx->tickets.ptr, 0, ctx->tickets.bytes) != cudaSuccess) {
+        cudaGetLastError();
+        parament_destroy(ctx);
+        return PARAMENT_ERR_CUDA;
+    }
+    *out = ctx;
+    return PARAMENT_OK;
+}
+
+int parament_destroy(parament_ctx *ctx) {
+    if (!ctx) return PARAMENT_OK;
+    {
+        DeviceGuard guard(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        cudaGetLastError();
+        Workspace *all[] = {&ctx->hraw, &ctx->full, &ctx->packed64, &ctx->packed32, &ctx->bnorm,
+                            &ctx->partials, &ctx->tickets, &ctx->counters, &ctx->status, &ctx->check,
+                            &ctx->ctrl_copy, &ctx->ctrl_conv, &ctx->uout};
+        for (Workspace *w : all) ws_free(*w);
+    }
+    delete ctx;
+    return PARAMENT_OK;
+}
+
+int parament_set_stream(parament_ctx *ctx, void *cuda_stream) {
+    if (!ctx) return PARAMENT_ERR_INVALID_VALUE;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    return PARAMENT_OK;
+}
+
+int parament_set_hamiltonians(parament_ctx *ctx, int dim, int n_ctrl, const void *H0, const void *Hk,
+                              parament_dtype dtype, parament_integrator integrator) {
+    if (!ctx) return PARAMENT_ERR_INVALID_VALUE;
+    ctx->err.clear();
+    if (dim < 1) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "dim must be >= 1 (got %d)", dim);
+    if (dim > kMaxDim)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "dim %d > %d is not supported by this build", dim, kMaxDim);
+    if (n_ctrl < 0 || n_ctrl > kMaxControls)
+        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "n_ctrl must be in [0, %d] (got %d)", kMaxControls, n_ctrl);
+    if (!H0 || (n_ctrl > 0 && !Hk)) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "null Hamiltonian pointer");
+    if (dtype != PARAMENT_C64 && dtype != PARAMENT_C128)
+        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown dtype %d", (int)dtype);
+    if (integrator != PARAMENT_MIDPOINT && integrator != PARAMENT_MAGNUS4_GL2 && integrator != PARAMENT_MAGNUS4_SIMPSON)
+        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown integrator %d", (int)integrator);
+    DeviceGuard guard(ctx->device);
+
+    const size_t esz = dtype == PARAMENT_C128 ? 16 : 8;
+    const size_t mat = (size_t)dim * dim * esz;
+    int st = ws_reserve(ctx, ctx->hraw, mat * (1 + n_ctrl));
+    if (st) return st;
+    // stage H0 and Hk contiguously: raw[0] = H0, raw[1 + k] = H_k
+    PM_CUDA(cudaMemcpyAsync(ctx->hraw.ptr, H0, mat, cudaMemcpyDefault, ctx->stream));
+    if (n_ctrl > 0)
+        PM_CUDA(cudaMemcpyAsync((char *)ctx->hraw.ptr + mat, Hk, mat * n_ctrl, cudaMemcpyDefault, ctx->stream));
+
+    // Hermiticity and finiteness of the inputs
+    PM_CUDA(cudaMemsetAsync(ctx->check.ptr, 0, ctx->check.bytes, ctx->stream));
+    if (dtype == PARAMENT_C128)
+        check_hermitian_kernel<double2><<<1 + n_ctrl, 256, 0, ctx->stream>>>(
+            (const double2 *)ctx->hraw.ptr, dim, 1 + n_ctrl, (unsigned long long *)ctx->check.ptr);
+    else
+        check_hermitian_kernel<float2><<<1 + n_ctrl, 256, 0, ctx->stream>>>(
+            (const float2 *)ctx->hraw.ptr, dim, 1 + n_ctrl, (unsigned long long *)ctx->check.ptr);
+    PM_CUDA(cudaGetLastError());
+    unsigned long long chk[3];
+    PM_CUDA(cudaMemcpyAsync(chk, ctx->check.ptr, sizeof(chk), cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    double herr, hmax;
+    std::memcpy(&herr, &chk[0], 8);
+    std::memcpy(&hmax, &chk[1], 8);
+    if (chk[2]) return set_err(ctx, PARAMENT_ERR_NONFINITE, "Hamiltonians contain NaN or Inf");
+    if (ctx->opt_check_herm && herr > (double)ctx->opt_herm_tol * 1e-12 * std::max(hmax, 1e-300))
+        return set_err(ctx, PARAMENT_ERR_NOT_HERMITIAN, "max |H - H^dagger| = %.3e exceeds tolerance (max |H| = %.3e)",
+                       herr, hmax);
+
+    const int Dp = pad_dim(dim);
+    const int nb = n_basis_for(n_ctrl, integrator);
+    const size_t DD = (size_t)Dp * Dp;
+    if ((st = ws_reserve(ctx, ctx->full, nb * DD * sizeof(double2)))) return st;
+    if ((st = ws_reserve(ctx, ctx->packed64, nb * DD * sizeof(double)))) return st;
+    if ((st = ws_reserve(ctx, ctx->packed32, nb * DD * sizeof(float)))) return st;
+    if ((st = ws_reserve(ctx, ctx->bnorm, nb * sizeof(double)))) return st;
+    if ((st = ws_reserve(ctx, ctx->partials, (size_t)ctx->max_grid * DD * sizeof(double2)))) return st;
+    const int magnus = integrator != PARAMENT_MIDPOINT;
+    if (dtype == PARAMENT_C128)
+        build_basis_kernel<double2><<<nb, 256, 0, ctx->stream>>>((const double2 *)ctx->hraw.ptr, dim, Dp, n_ctrl,
+                                                                 magnus, (double2 *)ctx->full.ptr);
+    else
+        build_basis_kernel<float2><<<nb, 256, 0, ctx->stream>>>((const float2 *)ctx->hraw.ptr, dim, Dp, n_ctrl,
+                                                                magnus, (double2 *)ctx->full.ptr);
+    PM_CUDA(cudaGetLastError());
+    pack_basis_kernel<<<nb, 256, 0, ctx->stream>>>((const double2 *)ctx->full.ptr, Dp, (double *)ctx->packed64.ptr,
+                                                   (float *)ctx->packed32.ptr, (double *)ctx->bnorm.ptr);
+    PM_CUDA(cudaGetLastError());
+
+    ctx->dim = dim;
+    ctx->dpad = Dp;
+    ctx->K = n_ctrl;
+    ctx->nb = nb;
+    ctx->dtype = dtype;
+    ctx->integ = integrator;
+    ctx->ctrl = nullptr;
+    ctx->state = 1;
+    return PARAMENT_OK;
+}
+
+int parament_set_controls(parament_ctx *ctx, const void *c, parament_real_dtype cdtype, int64_t n_steps, double dt) {
+    if (!ctx) return PARAMENT_ERR_INVALID_VALUE;
+    ctx->err.clear();
+    if (ctx->state < 1) return set_err(ctx, PARAMENT_ERR_STATE, "set_hamiltonians must come first");
+    if (cdtype != PARAMENT_F32 && cdtype != PARAMENT_F64)
+        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown control dtype %d", (int)cdtype);
+    if (n_steps < 0 || n_steps > (int64_t)0x7fffffff)
+        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "n_steps out of range (%lld)", (long long)n_steps);
+    if (!std::isfinite(dt)) return set_err(ctx, PARAMENT_ERR_NONFINITE, "dt is not finite");
+    const int64_t S = samples_for(n_steps, ctx->integ);
+    const size_t esz = cdtype == PARAMENT_F64 ? 8 : 4;
+    const size_t bytes = (size_t)ctx->K * (size_t)S * esz;
+    if (bytes > 0 && !c) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "null control pointer");
+    DeviceGuard guard(ctx->device);
+    const void *use = c;
+    if (bytes > 0 && !is_device_ptr(c)) {
+        int st = ws_reserve(ctx, ctx->ctrl_copy, bytes);
+        if (st) return st;
+        PM_CUDA(cudaMemcpyAsync(ctx->ctrl_copy.ptr, c, bytes, cudaMemcpyHostToDevice, ctx->stream));
+        use = ctx->ctrl_copy.ptr;
+    }
+    if (bytes > 0 && ((uintptr_t)use % esz))
+        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "control pointer not aligned to its element size");
+    ctx->ctrl = use;
+    ctx->cdtype = cdtype;
+    ctx->n_steps = n_steps;
+    ctx->S = S;
+    ctx->dt = dt;
+    ctx->state = 2;
+    return PARAMENT_OK;
+}
+
+int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) {
+    if (!ctx) return PARAMENT_ERR_INVALID_VALUE;
+    ctx->err.clear();
+    if (ctx->state < 2) return set_err(ctx, PARAMENT_ERR_STATE, "set_hamiltonians and set_controls must come first");
+    if (!U_out) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "null U_out");
+    if (prec == PARAMENT_PREC_FP32_TC_BF16X3 || prec == PARAMENT_PREC_FP32_TC_TF32X3)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "tensor-core precision modes need d >= 32; not in this build");
+    if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32)
+        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown precision %d", (int)prec);
+    DeviceGuard guard(ctx->device);
+    const int fp64 = prec == PARAMENT_PREC_FP64;
+    const int Dp = ctx->dpad, nb = ctx->nb;
+
+    // controls in the compute type
+    const void *ctrl = ctx->ctrl;
+    const int64_t count = (int64_t)ctx->K * ctx->S;
+    const bool want64 = fp64 != 0;
+    if (count > 0 && (ctx->cdtype == PARAMENT_F64) != want64) {
+        int st = ws_reserve(ctx, ctx->ctrl_conv, (size_t)count * (want64 ? 8 : 4));
+        if (st) return st;
+        const int blocks = (int)std::min<int64_t>((count + 255) / 256, 4096);
+        if (want64)
+            convert_kernel<float, double><<<blocks, 256, 0, ctx->stream>>>((const float *)ctrl,
+                                                                          (double *)ctx->ctrl_conv.ptr, count);
+        else
+            convert_kernel<double, float><<<blocks, 256, 0, ctx->stream>>>((const double *)ctrl,
+                                                                          (float *)ctx->ctrl_conv.ptr, count);
+        PM_CUDA(cudaGetLastError());
+        ctrl = ctx->ctrl_conv.ptr;
+    }
+
+    FusedParams p;
+    std::memset(&p, 0, sizeof(p));
+    const double u = fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+    if (build_classes(u, (int)ctx->opt_degree, p) <= 0)
+        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "Taylor degree %lld is not one of 1, 2, 4, 6, 9, 12",
+                       (long long)ctx->opt_degree);
+
+    // launch geometry
+    int warps = (int)ctx->opt_warps;
+    if (warps <= 0) {
+        warps = 8;
+        while (warps > 1 && fused_smem(Dp, fp64, nb, warps) > ctx->smem_optin) --warps;
+    }
+    if (warps > 8) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "at most 8 warps per block");
+    const size_t smem = fused_smem(Dp, fp64, nb, warps);
+    if (smem > ctx->smem_optin)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "basis of %d matrices (d=%d) needs %zu B shared memory > %zu",
+                       nb, ctx->dim, smem, ctx->smem_optin);
+    const int bps = fused_blocks_per_sm(Dp, fp64, (int)ctx->integ, warps, smem);
+    if (bps <= 0) return set_err(ctx, PARAMENT_ERR_CUDA, "occupancy query failed (%d warps, %zu B)", warps, smem);
+    const int leaves_per_block = warps * fused_gpw(Dp);
+    int grid = (int)ctx->opt_grid;
+    if (grid <= 0) {
+        const int64_t need = (ctx->n_steps + (int64_t)leaves_per_block * kLeafMinSteps - 1) /
+                             ((int64_t)leaves_per_block * kLeafMinSteps);
+        grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)bps * ctx->sm_count));
+    }
+    grid = std::min(grid, ctx->max_grid);
+
+    const size_t esz = ctx->dtype == PARAMENT_C128 ? 16 : 8;
+    const bool host_out = !is_device_ptr(U_out);
+    void *dst = U_out;
+    if (host_out) {
+        int st = ws_reserve(ctx, ctx->uout, (size_t)ctx->dim * ctx->dim * esz);
+        if (st) return st;
+        dst = ctx->uout.ptr;
+    } else if ((uintptr_t)U_out % esz) {
+        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "U_out not aligned to its element size");
+    }
+
+    p.ctrl = ctrl;
+    p.S = ctx->S;
+    p.n_steps = ctx->n_steps;
+    p.K = ctx->K;
+    p.n_basis = nb;
+    p.d_out = ctx->dim;
+    p.out_c128 = ctx->dtype == PARAMENT_C128;
+    p.dt = ctx->dt;
+    p.packed = fp64 ? ctx->packed64.ptr : ctx->packed32.ptr;
+    p.bnorm1 = (const double *)ctx->bnorm.ptr;
+    p.partials = (double2 *)ctx->partials.ptr;
+    p.tickets = (unsigned *)ctx->tickets.ptr;
+    p.U_out = dst;
+    p.counters = (unsigned long long *)ctx->counters.ptr;
+    p.status = (unsigned *)ctx->status.ptr;
+    p.extra_squarings = (int)ctx->opt_extra_sq;
+
+    PM_CUDA(fused_dispatch(Dp, fp64, (int)ctx->integ, p, grid, warps, smem, ctx->stream));
+
+    ctx->last = parament_stats{};
+    ctx->last.n_steps = ctx->n_steps;
+    ctx->last.dim = ctx->dim;
+    ctx->last.n_basis = nb;
+    ctx->last.grid_blocks = grid;
+    ctx->last.block_threads = warps * 32;
+    ctx->last.leaves = grid * leaves_per_block;
+    ctx->last.kernel_ms = -1.0;
+
+    if (host_out) {
+        PM_CUDA(cudaMemcpyAsync(U_out, dst, (size_t)ctx->dim * ctx->dim * esz, cudaMemcpyDeviceToHost, ctx->stream));
+        PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return PARAMENT_OK;
+}
+
+int parament_get_stats(parament_ctx *ctx, parament_stats *out) {
+    if (!ctx || !out) return PARAMENT_ERR_INVALID_VALUE;
+    DeviceGuard guard(ctx->device);
+    unsigned long long cnt[8];
+    unsigned stv[2];
+    PM_CUDA(cudaMemcpyAsync(cnt, ctx->counters.ptr, sizeof(cnt), cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaMemcpyAsync(stv, ctx->status.ptr, sizeof(stv), cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    parament_stats s = ctx->last;
+    s.exp_products = (int64_t)cnt[4];
+    s.tree_products = (int64_t)cnt[5];
+    s.max_degree = (int32_t)cnt[6];
+    s.max_squarings = (int32_t)cnt[7];
+    s.device_status = stv[1];
+    *out = s;
+    return PARAMENT_OK;
+}
+
+int parament_set_option(parament_ctx *ctx, int key, int64_t value) {
+    if (!ctx) return PARAMENT_ERR_INVALID_VALUE;
+    switch (key) {
+        case PARAMENT_OPT_TAYLOR_DEGREE:
+            if (value != 0 && value != 1 && value != 2 && value != 4 && value != 6 && value != 9 && value != 12)
+                return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "Taylor degree must be 0 or one of 1,2,4,6,9,12");
+            ctx->opt_degree = value;
+            return PARAMENT_OK;
+        case PARAMENT_OPT_GRID_BLOCKS:
+            if (value < 0 || value > ctx->max_grid)
+                return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "grid blocks must be in [0, %d]", ctx->max_grid);
+            ctx->opt_grid = value;
+            return PARAMENT_OK;
+        case PARAMENT_OPT_BLOCK_WARPS:
+            if (value < 0 || value > 8) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "block warps must be in [0, 8]");
+            ctx->opt_warps = value;
+            return PARAMENT_OK;
+        case PARAMENT_OPT_CHECK_HERMITIAN:
+            ctx->opt_check_herm = value != 0;
+            return PARAMENT_OK;
+        case PARAMENT_OPT_EXTRA_SQUARINGS:
+            if (value < 0 || value > 16) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "extra squarings in [0, 16]");
+            ctx->opt_extra_sq = value;
+            return PARAMENT_OK;
+        case PARAMENT_OPT_HERMITIAN_TOL_E12:
+            if (value < 0) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "tolerance must be >= 0");
+            ctx->opt_herm_tol = value;
+            return PARAMENT_OK;
+    }
+    return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown option key %d", key);
+}
+
+int parament_get_option(const parament_ctx *ctx, int key, int64_t *value) {
+    if (!ctx || !value) return PARAMENT_ERR_INVALID_VALUE;
+    switch (key) {
+        case PARAMENT_OPT_TAYLOR_DEGREE: *value = ctx->opt_degree; return PARAMENT_OK;
+        case PARAMENT_OPT_GRID_BLOCKS: *value = ctx->opt_grid; return PARAMENT_OK;
+        case PARAMENT_OPT_BLOCK_WARPS: *value = ctx->opt_warps; return PARAMENT_OK;
+        case PARAMENT_OPT_CHECK_HERMITIAN: *value = ctx->opt_check_herm; return PARAMENT_OK;
+        case PARAMENT_OPT_EXTRA_SQUARINGS: *value = ctx->opt_extra_sq; return PARAMENT_OK;
+        case PARAMENT_OPT_HERMITIAN_TOL_E12: *value = ctx->opt_herm_tol; return PARAMENT_OK;
+    }
+    return PARAMENT_ERR_INVALID_VALUE;
+}
+
+}  // extern "C"

@@ -1,0 +1,37 @@
+// Instantiations of the fused propagation kernel for padded dimension 2.
+#include "pm_fused.cuh"
+
+namespace pm {
+
+cudaError_t fused_dispatch_d2(int fp64, int integ, const FusedParams &p, int grid, int warps, size_t smem,
+                               cudaStream_t st) {
+    switch (integ * 2 + (fp64 ? 1 : 0)) {
+        case 0: return launch_fused<float, 2, kMidpoint>(p, grid, warps, smem, st);
+        case 1: return launch_fused<double, 2, kMidpoint>(p, grid, warps, smem, st);
+        case 2: return launch_fused<float, 2, kGL2>(p, grid, warps, smem, st);
+        case 3: return launch_fused<double, 2, kGL2>(p, grid, warps, smem, st);
+        case 4: return launch_fused<float, 2, kSimpson>(p, grid, warps, smem, st);
+        case 5: return launch_fused<double, 2, kSimpson>(p, grid, warps, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int fused_blocks_per_sm_d2(int fp64, int integ, int warps, size_t smem) {
+    switch (integ * 2 + (fp64 ? 1 : 0)) {
+        case 0: return fused_max_blocks_per_sm<float, 2, kMidpoint>(warps, smem);
+        case 1: return fused_max_blocks_per_sm<double, 2, kMidpoint>(warps, smem);
+        case 2: return fused_max_blocks_per_sm<float, 2, kGL2>(warps, smem);
+        case 3: return fused_max_blocks_per_sm<double, 2, kGL2>(warps, smem);
+        case 4: return fused_max_blocks_per_sm<float, 2, kSimpson>(warps, smem);
+        case 5: return fused_max_blocks_per_sm<double, 2, kSimpson>(warps, smem);
+    }
+    return 0;
+}
+
+size_t fused_smem_d2(int fp64, int n_basis, int warps) {
+    return fp64 ? fused_smem_bytes<double, 2>(n_basis, warps) : fused_smem_bytes<float, 2>(n_basis, warps);
+}
+
+int fused_groups_per_warp_d2() { return Geo<2>::GPW; }
+
+}  // namespace pm

@@ -1,0 +1,89 @@
+"""The C-ABI library loads and exports what include/parament.h declares; host-only logic.
+
+No compute calls here: these run without a GPU.
+"""
+
+import ctypes
+import math
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "parament.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(parament_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("parament_create", "parament_destroy", "parament_set_hamiltonians", "parament_set_controls",
+                     "parament_propagate"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2108_07126_gb300 import binding
+
+    lib = ctypes.CDLL(binding.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert binding.parament_version() == 1
+
+
+def test_status_strings():
+    from paper_2108_07126_gb300 import binding as b
+
+    assert b.parament_status_string(b.PARAMENT_OK) == "PARAMENT_OK"
+    assert b.parament_status_string(b.PARAMENT_ERR_STATE) == "PARAMENT_ERR_STATE"
+    assert b.parament_status_string(12345) == "PARAMENT_UNKNOWN_STATUS"
+
+
+def test_null_arguments_are_rejected_without_a_device():
+    from paper_2108_07126_gb300 import binding as b
+
+    assert b.raw_call("parament_destroy", None) == b.PARAMENT_OK
+    assert b.raw_call("parament_create", None, 0, None) == b.PARAMENT_ERR_INVALID_VALUE
+    assert b.raw_call("parament_propagate", None, None, 0) == b.PARAMENT_ERR_INVALID_VALUE
+    assert b.raw_call("parament_set_option", None, 1, 0) == b.PARAMENT_ERR_INVALID_VALUE
+
+
+def test_create_without_gpu_reports_cuda_error():
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_2108_07126_gb300 import binding as b
+
+    h = ctypes.c_void_p()
+    assert b.raw_call("parament_create", ctypes.byref(h), 0, None) == b.PARAMENT_ERR_CUDA
+    assert not h.value
+
+
+@pytest.mark.parametrize("m", [1, 2, 4, 6, 9, 12, 16, 20])
+@pytest.mark.parametrize("u", [2.0 ** -53, 2.0 ** -24])
+def test_taylor_theta_solves_the_remainder_bound(m, u):
+    """theta_m is the root of x^(m+1)/(m+1)! e^x = u, checked with 50-digit arithmetic."""
+    import mpmath
+
+    from paper_2108_07126_gb300 import binding as b
+
+    mpmath.mp.dps = 50
+    th = b.parament_taylor_theta(m, u)
+    f = lambda x: (m + 1) * mpmath.log(x) - mpmath.log(mpmath.factorial(m + 1)) + x - mpmath.log(u)
+    ref = mpmath.findroot(f, (mpmath.mpf("1e-30"), mpmath.mpf(50)), solver="illinois")
+    assert abs(th - float(ref)) <= 1e-12 * float(ref)
+    # monotone in m
+    assert b.parament_taylor_theta(m + 1, u) > th
+
+
+def test_taylor_theta_invalid():
+    from paper_2108_07126_gb300 import binding as b
+
+    assert b.parament_taylor_theta(0, 1e-16) < 0
+    assert b.parament_taylor_theta(3, 0.0) < 0

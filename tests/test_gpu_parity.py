@@ -1,0 +1,247 @@
+"""Parity of the CUDA propagator with the FP64 oracle, through the C ABI.
+
+Tolerances.  FP64 path: max-entry |U - U_oracle| <= 1e-11.  FP32 path: each
+slice contributes a rounding error of a few units of u = 2^-24 per entry
+times the dimension (assembly, Taylor polynomial, leaf product), and the N
+slice errors add up like a random walk, so the tests allow
+20 * u * d * sqrt(N) (plus the same for the oracle-side truncation of the
+inputs to float32), measured values are reported by the benchmark.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_07126_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+U32 = 2.0 ** -24
+
+
+def tol32(d, n):
+    return 20.0 * U32 * max(d, 2) * math.sqrt(max(n, 1)) + 1e-6
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    return torch
+
+
+@pytest.fixture()
+def prop(torch):
+    from paper_2108_07126_gb300.binding import Propagator
+
+    p = Propagator(0)
+    yield p
+    p.close()
+
+
+def run(prop, prob, prec="fp64", c_dtype=None, h_dtype=None):
+    import torch
+
+    hd = h_dtype or (torch.complex128 if prec == "fp64" else torch.complex64)
+    cd = c_dtype or (torch.float64 if prec == "fp64" else torch.float32)
+    prop.set_hamiltonians(torch.as_tensor(prob.H0).to(hd), torch.as_tensor(prob.Hk).to(hd), prob.integrator)
+    prop.set_controls(torch.as_tensor(prob.c).to(cd), prob.dt, prob.n_steps)
+    U = prop.propagate(prec)
+    torch.cuda.synchronize()
+    return U.cpu().numpy().astype(np.complex128)
+
+
+def ref(prob):
+    return oracle.propagate(prob.H0, prob.Hk, prob.c, prob.dt, prob.integrator)
+
+
+def ref32(prob):
+    """Oracle on the float32-rounded inputs the FP32 path sees."""
+    return oracle.propagate(prob.H0.astype(np.complex64).astype(np.complex128),
+                            prob.Hk.astype(np.complex64).astype(np.complex128),
+                            prob.c.astype(np.float32).astype(np.float64), prob.dt, prob.integrator)
+
+
+INTEGRATORS = ("midpoint", "magnus4_gl2", "magnus4_simpson")
+
+
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 6, 8, 12, 16])
+@pytest.mark.parametrize("n", [1, 37, 1000])
+def test_fp64_matches_oracle(prop, integrator, d, n):
+    prob = wl.random_problem(d, 3, n, integrator, seed=100 + d + n, g_norm=0.4)
+    U = run(prop, prob, "fp64")
+    assert np.max(np.abs(U - ref(prob))) <= TOL64
+
+
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+@pytest.mark.parametrize("d", [2, 3, 4, 8, 16])
+@pytest.mark.parametrize("n", [1, 37, 1000])
+def test_fp32_matches_oracle(prop, integrator, d, n):
+    prob = wl.random_problem(d, 3, n, integrator, seed=200 + d + n, g_norm=0.4)
+    U = run(prop, prob, "fp32")
+    assert np.max(np.abs(U - ref32(prob))) <= tol32(d, n)
+
+
+@pytest.mark.parametrize("g_norm", [1e-4, 0.05, 0.6, 2.5, 9.0, 40.0])
+@pytest.mark.parametrize("d", [2, 8, 16])
+def test_norm_range_uses_degree_and_squaring(prop, d, g_norm):
+    """Large exponents take squarings, tiny ones low degrees; both stay at FP64 accuracy."""
+    prob = wl.random_problem(d, 2, 19, "midpoint", seed=300 + d, g_norm=g_norm)
+    U = run(prop, prob, "fp64")
+    assert np.max(np.abs(U - ref(prob))) <= TOL64 * max(1.0, g_norm)
+    st = prop.stats()
+    assert st["tree_products"] == 19
+    if g_norm >= 9.0:
+        assert st["max_squarings"] >= 3
+    assert st["device_status"] == 0
+
+
+def test_empty_run_is_identity(prop):
+    prob = wl.random_problem(5, 2, 0, "magnus4_gl2", seed=1)
+    for prec in ("fp64", "fp32"):
+        U = run(prop, prob, prec)
+        assert np.array_equal(U, np.eye(5))
+
+
+def test_drift_only_is_exact_exponential(prop):
+    import scipy.linalg
+
+    rng = np.random.default_rng(7)
+    H0 = wl.random_hermitian(rng, 6)
+    prob = wl.Problem("drift", H0, np.zeros((0, 6, 6), np.complex128), np.zeros((0, 300)), 0.01, "midpoint", 300)
+    U = run(prop, prob, "fp64")
+    assert np.max(np.abs(U - scipy.linalg.expm(-1j * H0 * 3.0))) <= TOL64
+
+
+@pytest.mark.parametrize("grid", [1, 2, 3, 5, 7, 64, 152])
+@pytest.mark.parametrize("warps", [1, 3, 8])
+def test_tree_shapes_agree(prop, grid, warps):
+    """Any split of the slices over blocks, warps and leaves gives the same product."""
+    from paper_2108_07126_gb300 import binding as b
+
+    prob = wl.random_problem(4, 2, 4099, "magnus4_gl2", seed=11, g_norm=0.2)
+    prop.set_option(b.PARAMENT_OPT_GRID_BLOCKS, grid)
+    prop.set_option(b.PARAMENT_OPT_BLOCK_WARPS, warps)
+    U = run(prop, prob, "fp64")
+    assert np.max(np.abs(U - ref(prob))) <= TOL64
+    st = prop.stats()
+    assert st["grid_blocks"] == grid and st["block_threads"] == 32 * warps
+    assert st["tree_products"] == 4099
+
+
+def test_deterministic(prop):
+    prob = wl.random_problem(16, 4, 3001, "magnus4_gl2", seed=12, g_norm=0.3)
+    a = run(prop, prob, "fp32")
+    b = run(prop, prob, "fp32")
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("m", [1, 2, 4, 6, 9, 12])
+def test_forced_taylor_degree(prop, m):
+    from paper_2108_07126_gb300 import binding as b
+
+    prob = wl.random_problem(8, 2, 50, "midpoint", seed=13, g_norm=0.5)
+    prop.set_option(b.PARAMENT_OPT_TAYLOR_DEGREE, m)
+    U = run(prop, prob, "fp64")
+    assert np.max(np.abs(U - ref(prob))) <= TOL64
+    assert prop.stats()["max_degree"] == m
+
+
+def test_host_pointers(torch):
+    """Host arrays in, host U out, through the raw C entry points."""
+    from paper_2108_07126_gb300 import binding as b
+
+    prob = wl.random_problem(3, 2, 77, "magnus4_simpson", seed=14, g_norm=0.3)
+    ctx = b.parament_create(0, None)
+    try:
+        H0 = np.ascontiguousarray(prob.H0)
+        Hk = np.ascontiguousarray(prob.Hk)
+        c = np.ascontiguousarray(prob.c)
+        b.parament_set_hamiltonians(ctx, 3, 2, H0.ctypes.data, Hk.ctypes.data, b.PARAMENT_C128,
+                                    b.PARAMENT_MAGNUS4_SIMPSON)
+        b.parament_set_controls(ctx, c.ctypes.data, b.PARAMENT_F64, 77, prob.dt)
+        U = np.zeros((3, 3), np.complex128)
+        b.parament_propagate(ctx, U.ctypes.data, b.PARAMENT_PREC_FP64)
+        assert np.max(np.abs(U - ref(prob))) <= TOL64
+    finally:
+        b.parament_destroy(ctx)
+
+
+def test_state_machine_and_errors(prop, torch):
+    from paper_2108_07126_gb300 import binding as b
+
+    ctx = b.parament_create(0, None)
+    try:
+        U = torch.zeros(2, 2, dtype=torch.complex128, device="cuda")
+        st = b.raw_call("parament_propagate", ctx, U.data_ptr(), 0)
+        assert st == b.PARAMENT_ERR_STATE
+        H = torch.tensor([[1.0, 2.0], [3.0, 1.0]], dtype=torch.complex128, device="cuda")  # not Hermitian
+        st = b.raw_call("parament_set_hamiltonians", ctx, 2, 0, H.data_ptr(), None, 1, 0)
+        assert st == b.PARAMENT_ERR_NOT_HERMITIAN
+        Hn = torch.tensor([[float("nan"), 0.0], [0.0, 1.0]], dtype=torch.complex128, device="cuda")
+        assert b.raw_call("parament_set_hamiltonians", ctx, 2, 0, Hn.data_ptr(), None, 1, 0) == b.PARAMENT_ERR_NONFINITE
+        Hok = torch.eye(2, dtype=torch.complex128, device="cuda")
+        assert b.raw_call("parament_set_hamiltonians", ctx, 0, 0, Hok.data_ptr(), None, 1, 0) == \
+            b.PARAMENT_ERR_INVALID_VALUE
+        assert b.raw_call("parament_set_hamiltonians", ctx, 64, 0, Hok.data_ptr(), None, 1, 0) == \
+            b.PARAMENT_ERR_UNSUPPORTED
+        assert b.raw_call("parament_set_controls", ctx, None, 1, 4, 0.1) == b.PARAMENT_ERR_STATE
+        assert b.raw_call("parament_set_hamiltonians", ctx, 2, 0, Hok.data_ptr(), None, 1, 0) == b.PARAMENT_OK
+        assert b.raw_call("parament_propagate", ctx, U.data_ptr(), 0) == b.PARAMENT_ERR_STATE
+        assert b.raw_call("parament_set_controls", ctx, None, 1, -1, 0.1) == b.PARAMENT_ERR_INVALID_VALUE
+        assert b.raw_call("parament_set_controls", ctx, None, 1, 4, 0.5) == b.PARAMENT_OK
+        assert b.raw_call("parament_propagate", ctx, U.data_ptr(), 2) == b.PARAMENT_ERR_UNSUPPORTED
+        assert b.raw_call("parament_propagate", ctx, U.data_ptr(), 0) == b.PARAMENT_OK
+        torch.cuda.synchronize()
+        ref_u = np.diag(np.exp(-1j * np.ones(2) * 2.0))
+        assert np.max(np.abs(U.cpu().numpy() - ref_u)) <= TOL64
+        assert b.raw_call("parament_set_option", ctx, 999, 0) == b.PARAMENT_ERR_INVALID_VALUE
+        assert b.raw_call("parament_set_option", ctx, b.PARAMENT_OPT_TAYLOR_DEGREE, 5) == b.PARAMENT_ERR_INVALID_VALUE
+    finally:
+        b.parament_destroy(ctx)
+
+
+def test_nonfinite_controls_flagged(prop):
+    prob = wl.random_problem(4, 2, 40, "midpoint", seed=15)
+    prob.c[1, 17] = np.nan
+    run(prop, prob, "fp64")
+    assert prop.stats()["device_status"] & 0x1
+
+
+def test_mixed_control_dtypes(prop, torch):
+    prob = wl.random_problem(4, 2, 200, "magnus4_gl2", seed=16, g_norm=0.3)
+    U = run(prop, prob, "fp64", c_dtype=torch.float32)
+    r = oracle.propagate(prob.H0, prob.Hk, prob.c.astype(np.float32).astype(np.float64), prob.dt, prob.integrator)
+    assert np.max(np.abs(U - r)) <= TOL64
+    U = run(prop, prob, "fp32", c_dtype=torch.float64, h_dtype=torch.complex128)
+    assert np.max(np.abs(U - ref(prob))) <= tol32(4, 200)
+
+
+# --- the benchmark workloads -------------------------------------------------------------------
+
+
+def test_rabi_qubit_full_size(prop):
+    """Driven two-level system at N = 2^14: oracle parity, unitarity, RWA population."""
+    prob = wl.rabi_qubit()
+    U = run(prop, prob, "fp64")
+    R = ref(prob)
+    assert np.max(np.abs(U - R)) <= TOL64
+    assert np.max(np.abs(U.conj().T @ U - np.eye(2))) <= 1e-12
+    assert abs(U[1, 0]) ** 2 < 0.05
+    U32 = run(prop, prob, "fp32")
+    assert np.max(np.abs(U32 - R)) <= tol32(2, prob.n_steps)
+
+
+def test_coupled_spins_slice_of_run(prop):
+    """Four coupled spins, GL4, first 2^15 slices of the workload."""
+    full = wl.coupled_spins(n_steps=1 << 15)
+    U = run(prop, full, "fp64")
+    R = ref(full)
+    assert np.max(np.abs(U - R)) <= TOL64
+    U32 = run(prop, full, "fp32", h_dtype=None)
+    assert np.max(np.abs(U32 - ref32(full))) <= tol32(16, full.n_steps)
