@@ -183,7 +183,7 @@ def run_reference(args):
 
 def workload_config(n_steps, prec):
     return {"workload": f"coupled_spins_d16_magnus4_gl2_N{n_steps}", "dim": 16, "n_steps": n_steps, "n_ctrl": 8,
-            "n_basis": 45, "integrator": "magnus4_gl2", "precision": prec,
+            "n_coefficients": 45, "integrator": "magnus4_gl2", "precision": prec,
             "l2": f"flushed by a {L2_FLUSH_BYTES >> 20} MiB write between timed steps"}
 
 
@@ -304,7 +304,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(workload_config(N, "fp32"), parallelism=("replicas" if world > 1 else "single")),
+        "config": dict(workload_config(N, "fp32"), parallelism=("replicas" if world > 1 else "single"),
+                       n_basis_kept=st32["n_basis"]),
         "fp64_gpu": {"value": world * N / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
                      "steps": args.fp64_steps, "max_abs_err_vs_oracle_bound": 1e-11,
                      "unitarity_err": unit_err, "exp_products": st64["exp_products"],

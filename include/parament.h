@@ -203,6 +203,17 @@ int parament_get_option(const parament_ctx *ctx, int key, int64_t *value);
  */
 double parament_taylor_theta(int m, double u);
 
+/*
+ * Degree m and squarings s the kernels use for a slice whose norm bound is
+ * `norm_bound` (>= ||G||_1), at unit roundoff u (2^-53 for FP64, 2^-24 for
+ * FP32): among m in {1, 2, 4, 6, 9, 12} (Paterson-Stockmeyer products
+ * 0, 1, 2, 3, 4, 5) and s >= 0 with norm_bound / 2^s <= theta_m(u / 2^s), the
+ * pair with the fewest complex products (PS products + s).  force_m = 0 lets
+ * m vary, otherwise m = force_m.  Host-only helper (no GPU needed).
+ * Errors: INVALID_VALUE for bad arguments, UNSUPPORTED if no s <= 62 suffices.
+ */
+int parament_taylor_choice(double norm_bound, double u, int force_m, int *m_out, int *s_out);
+
 /* Static text for a status code. */
 const char *parament_status_string(int status);
 

@@ -102,6 +102,8 @@ _SIGS = {
     "parament_set_option": ([_vp, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
     "parament_get_option": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "parament_taylor_theta": ([ctypes.c_int, ctypes.c_double], ctypes.c_double),
+    "parament_taylor_choice": ([ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "parament_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "parament_last_error": ([_vp], ctypes.c_char_p),
 }
@@ -182,6 +184,13 @@ def parament_get_option(ctx, key: int) -> int:
 
 def parament_taylor_theta(m: int, u: float) -> float:
     return _lib.parament_taylor_theta(int(m), float(u))
+
+
+def parament_taylor_choice(norm_bound: float, u: float, force_m: int = 0) -> tuple[int, int]:
+    m = ctypes.c_int()
+    s = ctypes.c_int()
+    _check(_lib.parament_taylor_choice(float(norm_bound), float(u), int(force_m), ctypes.byref(m), ctypes.byref(s)))
+    return m.value, s.value
 
 
 def raw_call(name: str, *args) -> int:

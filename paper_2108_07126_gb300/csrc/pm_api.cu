@@ -19,7 +19,7 @@ namespace pm {
     cudaError_t fused_dispatch_d##D(int, int, const FusedParams &, int, int, size_t, cudaStream_t);      \
     int fused_blocks_per_sm_d##D(int, int, int, size_t);                                                 \
     size_t fused_smem_d##D(int, int, int);                                                               \
-    int fused_groups_per_warp_d##D();
+    int fused_groups_per_warp_d##D(int);
 PM_DECL_D(2)
 PM_DECL_D(4)
 PM_DECL_D(8)
@@ -54,7 +54,9 @@ struct parament_ctx {
     parament_integrator integ = PARAMENT_MIDPOINT;
 
     Workspace hraw, full, packed64, packed32, bnorm, partials, tickets, counters, status, check;
-    Workspace ctrl_copy, ctrl_conv, uout;
+    Workspace ctrl_copy, ctrl_conv, uout, bmax, cpacked64, cpacked32, cbnorm;
+    int nb_eff = 0;
+    std::vector<short> slot_of;
 
     const void *ctrl = nullptr;
     parament_real_dtype cdtype = PARAMENT_F64;
@@ -230,7 +232,8 @@ __global__ void build_basis_kernel(const InT *raw, int d, int Dp, int K, int mag
 
 // Packed real form of each Hermitian basis matrix (upper triangle: real parts,
 // strictly lower triangle: imaginary parts) and its FP64 1-norm.
-__global__ void pack_basis_kernel(const double2 *full, int Dp, double *p64, float *p32, double *bnorm) {
+__global__ void pack_basis_kernel(const double2 *full, int Dp, double *p64, float *p32, double *bnorm,
+                                  double *bmax) {
     const int e = blockIdx.x;
     const double2 *B = full + (size_t)e * Dp * Dp;
     for (int t = threadIdx.x; t < Dp * Dp; t += blockDim.x) {
@@ -240,16 +243,25 @@ __global__ void pack_basis_kernel(const double2 *full, int Dp, double *p64, floa
         p64[(size_t)e * Dp * Dp + t] = x;
         p32[(size_t)e * Dp * Dp + t] = (float)x;
     }
-    __shared__ double colsum[kMaxDim];
+    __shared__ double colsum[kMaxDim], colmax[kMaxDim];
     if (threadIdx.x < Dp) {
-        double s = 0.0;
-        for (int i = 0; i < Dp; ++i) s += hypot(B[i * Dp + threadIdx.x].x, B[i * Dp + threadIdx.x].y);
+        double s = 0.0, mx = 0.0;
+        for (int i = 0; i < Dp; ++i) {
+            const double a = hypot(B[i * Dp + threadIdx.x].x, B[i * Dp + threadIdx.x].y);
+            s += a;
+            mx = fmax(mx, a);
+        }
         colsum[threadIdx.x] = s;
+        colmax[threadIdx.x] = mx;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double m = 0.0;
-        for (int j = 0; j < Dp; ++j) m = fmax(m, colsum[j]);
+        double m = 0.0, mx = 0.0;
+        for (int j = 0; j < Dp; ++j) {
+            m = fmax(m, colsum[j]);
+            mx = fmax(mx, colmax[j]);
+        }
+        bmax[e] = mx;
         // the packed FP32 basis is a rounded copy: widen the bound by its relative rounding
         bnorm[e] = m * (1.0 + 4.0 * 5.960464477539063e-08 * Dp);
     }
@@ -276,7 +288,10 @@ int build_classes(double u, int force_m, FusedParams &p) {
         for (const auto &dg : kDegrees) {
             const int m = dg[0], q = dg[1], r = dg[2];
             if (force_m > 0 && m != force_m) continue;
-            const double th = parament_taylor_theta(m, u);
+            // s squarings multiply the truncation error of exp(A / 2^s) by 2^s: the
+            // polynomial must meet u / 2^s so that the squared result meets u.
+            const double th = parament_taylor_theta(m, std::ldexp(u, -s));
+            if (!(th > 0.0)) continue;
             all.push_back({std::ldexp(th, s), (q - 1) + (r - 1) + s, m, q, r, s});
         }
     }
@@ -335,12 +350,12 @@ size_t fused_smem(int Dp, int fp64, int nb, int warps) {
     }
     return 0;
 }
-int fused_gpw(int Dp) {
+int fused_gpw(int Dp, int fp64) {
     switch (Dp) {
-        case 2: return fused_groups_per_warp_d2();
-        case 4: return fused_groups_per_warp_d4();
-        case 8: return fused_groups_per_warp_d8();
-        case 16: return fused_groups_per_warp_d16();
+        case 2: return fused_groups_per_warp_d2(fp64);
+        case 4: return fused_groups_per_warp_d4(fp64);
+        case 8: return fused_groups_per_warp_d8(fp64);
+        case 16: return fused_groups_per_warp_d16(fp64);
     }
     return 1;
 }
@@ -382,6 +397,22 @@ double parament_taylor_theta(int m, double u) {
         if (g(mid) <= 0.0) lo = mid; else hi = mid;
     }
     return lo;
+}
+
+int parament_taylor_choice(double norm_bound, double u, int force_m, int *m_out, int *s_out) {
+    if (!m_out || !s_out || !(u > 0.0) || !(u < 1.0) || !(norm_bound >= 0.0) || std::isinf(norm_bound))
+        return PARAMENT_ERR_INVALID_VALUE;
+    if (force_m != 0 && force_m != 1 && force_m != 2 && force_m != 4 && force_m != 6 && force_m != 9 && force_m != 12)
+        return PARAMENT_ERR_INVALID_VALUE;
+    FusedParams p;
+    std::memset(&p, 0, sizeof(p));
+    if (build_classes(u, force_m, p) <= 0) return PARAMENT_ERR_INVALID_VALUE;
+    int c = 0;
+    while (c < p.n_cls - 1 && !(norm_bound <= p.cls_cap[c])) ++c;
+    if (!(norm_bound <= p.cls_cap[c])) return PARAMENT_ERR_UNSUPPORTED;
+    *m_out = cls_m(p.cls_code[c]);
+    *s_out = cls_s(p.cls_code[c]);
+    return PARAMENT_OK;
 }
 
 int parament_create(parament_ctx **out, int device, void *cuda_stream) {
@@ -434,7 +465,8 @@ int parament_destroy(parament_ctx *ctx) {
         cudaGetLastError();
         Workspace *all[] = {&ctx->hraw, &ctx->full, &ctx->packed64, &ctx->packed32, &ctx->bnorm,
                             &ctx->partials, &ctx->tickets, &ctx->counters, &ctx->status, &ctx->check,
-                            &ctx->ctrl_copy, &ctx->ctrl_conv, &ctx->uout};
+                            &ctx->ctrl_copy, &ctx->ctrl_conv, &ctx->uout, &ctx->bmax, &ctx->cpacked64,
+                            &ctx->cpacked32, &ctx->cbnorm};
         for (Workspace *w : all) ws_free(*w);
     }
     delete ctx;
@@ -508,9 +540,35 @@ int parament_set_hamiltonians(parament_ctx *ctx, int dim, int n_ctrl, const void
         build_basis_kernel<float2><<<nb, 256, 0, ctx->stream>>>((const float2 *)ctx->hraw.ptr, dim, Dp, n_ctrl,
                                                                 magnus, (double2 *)ctx->full.ptr);
     PM_CUDA(cudaGetLastError());
+    if ((st = ws_reserve(ctx, ctx->bmax, nb * sizeof(double)))) return st;
     pack_basis_kernel<<<nb, 256, 0, ctx->stream>>>((const double2 *)ctx->full.ptr, Dp, (double *)ctx->packed64.ptr,
-                                                   (float *)ctx->packed32.ptr, (double *)ctx->bnorm.ptr);
+                                                   (float *)ctx->packed32.ptr, (double *)ctx->bnorm.ptr,
+                                                   (double *)ctx->bmax.ptr);
     PM_CUDA(cudaGetLastError());
+
+    // Identically zero basis matrices (e.g. commutators of controls acting on
+    // different subsystems) contribute nothing to G_j: keep only the others.
+    std::vector<double> bmax(nb);
+    PM_CUDA(cudaMemcpyAsync(bmax.data(), ctx->bmax.ptr, nb * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->slot_of.assign(kMaxBasis, (short)-1);
+    int kept = 0;
+    for (int e = 0; e < nb; ++e)
+        if (bmax[e] > 0.0) ctx->slot_of[e] = (short)kept++;
+    if ((st = ws_reserve(ctx, ctx->cpacked64, std::max(kept, 1) * DD * sizeof(double)))) return st;
+    if ((st = ws_reserve(ctx, ctx->cpacked32, std::max(kept, 1) * DD * sizeof(float)))) return st;
+    if ((st = ws_reserve(ctx, ctx->cbnorm, std::max(kept, 1) * sizeof(double)))) return st;
+    for (int e = 0; e < nb; ++e) {
+        const int sl = ctx->slot_of[e];
+        if (sl < 0) continue;
+        PM_CUDA(cudaMemcpyAsync((double *)ctx->cpacked64.ptr + sl * DD, (double *)ctx->packed64.ptr + e * DD,
+                                DD * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+        PM_CUDA(cudaMemcpyAsync((float *)ctx->cpacked32.ptr + sl * DD, (float *)ctx->packed32.ptr + e * DD,
+                                DD * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+        PM_CUDA(cudaMemcpyAsync((double *)ctx->cbnorm.ptr + sl, (double *)ctx->bnorm.ptr + e, sizeof(double),
+                                cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    ctx->nb_eff = kept;
 
     ctx->dim = dim;
     ctx->dpad = Dp;
@@ -566,7 +624,7 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) 
         return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown precision %d", (int)prec);
     DeviceGuard guard(ctx->device);
     const int fp64 = prec == PARAMENT_PREC_FP64;
-    const int Dp = ctx->dpad, nb = ctx->nb;
+    const int Dp = ctx->dpad, nb = ctx->nb_eff;
 
     // controls in the compute type
     const void *ctrl = ctx->ctrl;
@@ -606,7 +664,7 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) 
                        nb, ctx->dim, smem, ctx->smem_optin);
     const int bps = fused_blocks_per_sm(Dp, fp64, (int)ctx->integ, warps, smem);
     if (bps <= 0) return set_err(ctx, PARAMENT_ERR_CUDA, "occupancy query failed (%d warps, %zu B)", warps, smem);
-    const int leaves_per_block = warps * fused_gpw(Dp);
+    const int leaves_per_block = warps * fused_gpw(Dp, fp64);
     int grid = (int)ctx->opt_grid;
     if (grid <= 0) {
         const int64_t need = (ctx->n_steps + (int64_t)leaves_per_block * kLeafMinSteps - 1) /
@@ -631,11 +689,13 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) 
     p.n_steps = ctx->n_steps;
     p.K = ctx->K;
     p.n_basis = nb;
+    p.n_coef = ctx->nb;
+    for (int e = 0; e < kMaxBasis; ++e) p.slot_of[e] = ctx->slot_of[e];
     p.d_out = ctx->dim;
     p.out_c128 = ctx->dtype == PARAMENT_C128;
     p.dt = ctx->dt;
-    p.packed = fp64 ? ctx->packed64.ptr : ctx->packed32.ptr;
-    p.bnorm1 = (const double *)ctx->bnorm.ptr;
+    p.packed = fp64 ? ctx->cpacked64.ptr : ctx->cpacked32.ptr;
+    p.bnorm1 = (const double *)ctx->cbnorm.ptr;
     p.partials = (double2 *)ctx->partials.ptr;
     p.tickets = (unsigned *)ctx->tickets.ptr;
     p.U_out = dst;

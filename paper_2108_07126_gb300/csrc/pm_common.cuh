@@ -33,6 +33,7 @@ __device__ __forceinline__ void cfma(C &acc, const C a, const C b) {
 constexpr int kMaxClasses = 96;
 constexpr int kMaxDegree = 12;  // q <= 3 powers: m in {1, 2, 4, 6, 9, 12}
 constexpr int kMaxControls = 16;
+constexpr int kMaxBasis = 1 + 2 * kMaxControls + kMaxControls * (kMaxControls - 1) / 2;
 
 __host__ __device__ inline int cls_m(int code) { return code & 0xff; }
 __host__ __device__ inline int cls_q(int code) { return (code >> 8) & 0xff; }
@@ -54,7 +55,8 @@ struct FusedParams {
     int64_t S;                 // samples per control (row stride of ctrl)
     int64_t n_steps;
     int K;
-    int n_basis;
+    int n_basis;               // basis matrices kept in the kernel (identically zero ones dropped)
+    int n_coef;                // effective coefficients per slice: 1 + K or 1 + K (K + 3) / 2
     int d_out;                 // true dimension (<= padded D)
     int out_c128;              // U_out is complex128 (else complex64)
     double dt;
@@ -69,6 +71,7 @@ struct FusedParams {
     int n_cls;
     double cls_cap[kMaxClasses];
     int cls_code[kMaxClasses];
+    short slot_of[kMaxBasis];  // coefficient index -> kept basis slot, -1 if the matrix is zero
     double coef_d[kMaxDegree + 1];  // 1/k!
     float coef_f[kMaxDegree + 1];
 };

@@ -13,6 +13,10 @@
 //   5. block partials combined pairwise in FP64 through global memory: the
 //      second block to arrive at a tree node multiplies, the first leaves.
 //      No block ever waits for another one.
+//
+// Shared-memory layout per block: the packed basis (row stride D) and its
+// norms, then per warp: GPW groups x 4 complex D x LD slots (X / Horner
+// operand, X^2, X^3, leaf product R), the coefficient tile and class tile.
 #pragma once
 
 #include "pm_common.cuh"
@@ -20,32 +24,42 @@
 namespace pm {
 
 // Lane tiling of one D x D complex product over the LANES lanes of a group.
-// Lane (rb, cb) owns rows rb + r * (D/TR) and columns cb + c * (D/TC).
-template <int D> struct Tiling;
-template <> struct Tiling<2> { static constexpr int LANES = 1, TR = 2, TC = 2, LD = 2; };
-template <> struct Tiling<4> { static constexpr int LANES = 2, TR = 2, TC = 4, LD = 4; };
-template <> struct Tiling<8> { static constexpr int LANES = 8, TR = 2, TC = 4, LD = 9; };
-template <> struct Tiling<16> { static constexpr int LANES = 32, TR = 2, TC = 4, LD = 17; };
+// Lane (rb, cb) owns rows rb + r * RBN (r < TR) and columns col(cb, c) (c < TC);
+// V complex numbers move per shared-memory access (V = 2: 16-byte float4).
+template <typename Real, int D> struct Tiling;
+template <> struct Tiling<float, 16> { static constexpr int LANES = 16, TR = 4, TC = 4, LD = 20, V = 2, GPAD = 16; };
+template <> struct Tiling<float, 8> { static constexpr int LANES = 4, TR = 4, TC = 4, LD = 8, V = 2, GPAD = 16; };
+template <> struct Tiling<float, 4> { static constexpr int LANES = 1, TR = 4, TC = 4, LD = 4, V = 2, GPAD = 16; };
+template <> struct Tiling<float, 2> { static constexpr int LANES = 1, TR = 2, TC = 2, LD = 2, V = 2, GPAD = 16; };
+template <> struct Tiling<double, 16> { static constexpr int LANES = 32, TR = 2, TC = 4, LD = 17, V = 1, GPAD = 0; };
+template <> struct Tiling<double, 8> { static constexpr int LANES = 8, TR = 2, TC = 4, LD = 9, V = 1, GPAD = 16; };
+template <> struct Tiling<double, 4> { static constexpr int LANES = 2, TR = 2, TC = 4, LD = 4, V = 1, GPAD = 16; };
+template <> struct Tiling<double, 2> { static constexpr int LANES = 1, TR = 2, TC = 2, LD = 2, V = 1, GPAD = 16; };
 
-template <int D> struct Geo {
-    using T = Tiling<D>;
-    static constexpr int LANES = T::LANES, TR = T::TR, TC = T::TC, LD = T::LD;
-    static constexpr int GPW = 32 / LANES;   // groups per warp
-    static constexpr int RBN = D / TR;       // row stride of a lane's rows
-    static constexpr int CBN = D / TC;       // column stride of a lane's columns
+template <typename Real, int D> struct Geo {
+    using T = Tiling<Real, D>;
+    using C = typename Cx<Real>::T;
+    static constexpr int LANES = T::LANES, TR = T::TR, TC = T::TC, LD = T::LD, V = T::V;
+    static constexpr int GPW = 32 / LANES;        // groups per warp
+    static constexpr int RBN = D / TR;            // row blocks: rows rb + r * RBN
+    static constexpr int CBW = D / TC;            // column blocks
     static constexpr int DD = D * D;
-    static constexpr int SLOT = ((D * LD + 1) / 2) * 2;  // complex elements per slot, even
-    static constexpr int NSLOT = 5;                      // X, X^2, X^3, T (work), R (leaf product)
+    static constexpr int SLOT = D * LD;           // complex elements per slot
+    static constexpr int NSLOT = 4;               // X (then Horner operand), X^2, X^3, R
+    static constexpr int GSTRIDE = NSLOT * SLOT * (int)sizeof(C) + T::GPAD;  // bytes per group
+    static constexpr int NCH = DD / (4 * LANES);  // 4-entry chunks of the packed exponent per lane
+    static constexpr int PS = (D >= 4) ? D + 1 : D;  // row stride of the packed exponent scratch
+    static_assert(LANES == RBN * CBW, "tiling must cover the matrix");
+    static_assert(NCH >= 1 && NCH * 4 * LANES == DD, "assembly chunks must cover the matrix");
+    static_assert(TC % V == 0 && LD % V == 0, "vector accesses must stay aligned");
+    __host__ __device__ static constexpr int col(int cb, int c) { return V == 2 ? cb * TC + c : cb + c * CBW; }
 };
 
-// smem bytes of one warp's workspace for a given basis size
 template <typename Real, int D>
 __host__ __device__ inline size_t warp_ws_bytes(int n_basis) {
-    using G = Geo<D>;
-    size_t slots = (size_t)G::GPW * G::NSLOT * G::SLOT * sizeof(typename Cx<Real>::T);
-    size_t gam = (size_t)n_basis * 32 * sizeof(Real);
-    size_t cls = 32 * sizeof(int);
-    return (slots + gam + cls + 15) & ~(size_t)15;
+    using G = Geo<Real, D>;
+    size_t b = (size_t)G::GPW * G::GSTRIDE + (size_t)n_basis * 32 * sizeof(Real) + 32 * sizeof(int);
+    return (b + 15) & ~(size_t)15;
 }
 
 template <typename Real, int D>
@@ -59,44 +73,84 @@ __host__ __device__ inline size_t fused_smem_bytes(int n_basis, int warps) {
     return basis_smem_bytes<Real, D>(n_basis) + (size_t)warps * warp_ws_bytes<Real, D>(n_basis);
 }
 
+// ---------------------------------------------------------------- tile primitives
+
+template <typename C, int V> struct Vec;
+template <> struct Vec<float2, 2> {
+    __device__ static inline void ld(const float2 *p, float2 (&o)[2]) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        o[0] = make_float2(v.x, v.y);
+        o[1] = make_float2(v.z, v.w);
+    }
+    __device__ static inline void st(float2 *p, const float2 a, const float2 b) {
+        *reinterpret_cast<float4 *>(p) = make_float4(a.x, a.y, b.x, b.y);
+    }
+};
+template <typename C> struct Vec<C, 1> {
+    __device__ static inline void ld(const C *p, C (&o)[1]) { o[0] = *p; }
+};
+
 // acc = A * B for the lane's tile; A, B are D x D complex matrices with row stride LD
 template <typename Real, int D>
 __device__ __forceinline__ void mm_tile(const typename Cx<Real>::T *__restrict__ A,
                                         const typename Cx<Real>::T *__restrict__ B, int rb, int cb,
-                                        typename Cx<Real>::T (&acc)[Geo<D>::TR][Geo<D>::TC]) {
-    using G = Geo<D>;
-    using C = typename Cx<Real>::T;
+                                        typename Cx<Real>::T (&acc)[Geo<Real, D>::TR][Geo<Real, D>::TC]) {
+    using G = Geo<Real, D>;
+    using C = typename G::C;
+    constexpr int TR = G::TR, TC = G::TC, V = G::V, LD = G::LD;
 #pragma unroll
-    for (int r = 0; r < G::TR; ++r)
+    for (int r = 0; r < TR; ++r)
 #pragma unroll
-        for (int c = 0; c < G::TC; ++c) acc[r][c] = Cx<Real>::make(0, 0);
+        for (int c = 0; c < TC; ++c) acc[r][c] = Cx<Real>::make(0, 0);
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-        C a[G::TR], b[G::TC];
+    for (int k = 0; k < D; k += V) {
+        C a[TR][V], b[V][TC];
 #pragma unroll
-        for (int r = 0; r < G::TR; ++r) a[r] = A[(rb + r * G::RBN) * G::LD + k];
+        for (int r = 0; r < TR; ++r) Vec<C, V>::ld(A + (rb + r * G::RBN) * LD + k, a[r]);
 #pragma unroll
-        for (int c = 0; c < G::TC; ++c) b[c] = B[k * G::LD + cb + c * G::CBN];
+        for (int v = 0; v < V; ++v)
 #pragma unroll
-        for (int r = 0; r < G::TR; ++r)
+            for (int c = 0; c < TC; c += V) {
+                C t[V];
+                Vec<C, V>::ld(B + (k + v) * LD + G::col(cb, c), t);
 #pragma unroll
-            for (int c = 0; c < G::TC; ++c) cfma(acc[r][c], a[r], b[c]);
+                for (int w = 0; w < V; ++w) b[v][c + w] = t[w];
+            }
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int c = 0; c < TC; ++c) cfma(acc[r][c], a[r][v], b[v][c]);
     }
 }
 
 template <typename Real, int D>
 __device__ __forceinline__ void st_tile(typename Cx<Real>::T *S, int rb, int cb,
-                                        const typename Cx<Real>::T (&t)[Geo<D>::TR][Geo<D>::TC]) {
-    using G = Geo<D>;
+                                        const typename Cx<Real>::T (&t)[Geo<Real, D>::TR][Geo<Real, D>::TC]) {
+    using G = Geo<Real, D>;
 #pragma unroll
-    for (int r = 0; r < G::TR; ++r)
+    for (int r = 0; r < G::TR; ++r) {
+        if constexpr (G::V == 2) {
 #pragma unroll
-        for (int c = 0; c < G::TC; ++c) S[(rb + r * G::RBN) * G::LD + cb + c * G::CBN] = t[r][c];
+            for (int c = 0; c < G::TC; c += 2)
+                Vec<float2, 2>::st(S + (rb + r * G::RBN) * G::LD + G::col(cb, c), t[r][c], t[r][c + 1]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < G::TC; ++c) S[(rb + r * G::RBN) * G::LD + G::col(cb, c)] = t[r][c];
+        }
+    }
 }
 
 template <typename Real> __device__ __forceinline__ Real coef(const FusedParams &p, int k);
 template <> __device__ __forceinline__ float coef<float>(const FusedParams &p, int k) { return p.coef_f[k]; }
 template <> __device__ __forceinline__ double coef<double>(const FusedParams &p, int k) { return p.coef_d[k]; }
+
+template <typename Real> __device__ __forceinline__ Real pow2neg(int s);
+template <> __device__ __forceinline__ float pow2neg<float>(int s) { return __int_as_float((127 - s) << 23); }
+template <> __device__ __forceinline__ double pow2neg<double>(int s) {
+    return __longlong_as_double((long long)(1023 - s) << 52);
+}
 
 // Effective coefficients gamma_e of one slice (Sec. 4, Eq. magnus_coeffs with the
 // commutator sign of Omega_2): basis order H0, H_k, i[H0,H_k], i[H_k,H_k'] (k < k').
@@ -110,37 +164,40 @@ __device__ __forceinline__ void slice_coefficients(const FusedParams &p, int64_t
         for (int e = 0; e < p.n_basis; ++e) gam[e * 32] = Real(0);
         return;
     }
-    gam[0] = h;
+    // coefficients of identically zero basis matrices are dropped
+    auto put = [&](int e, Real v) {
+        const int sl = p.slot_of[e];
+        if (sl >= 0) gam[sl * 32] = v;
+    };
+    put(0, h);
     if (INTEG == kMidpoint) {
-        for (int k = 0; k < K; ++k) gam[(1 + k) * 32] = h * c[(int64_t)k * p.S + j];
+        for (int k = 0; k < K; ++k) put(1 + k, h * c[(int64_t)k * p.S + j]);
         return;
     }
     Real c1[kMaxControls], c2[kMaxControls];
-    Real w1, wc;  // weight of the averaged controls and of the commutators
+    Real wc;  // weight of the commutator coefficients
     if (INTEG == kGL2) {
         for (int k = 0; k < K; ++k) {
             c1[k] = c[(int64_t)k * p.S + 2 * j];
             c2[k] = c[(int64_t)k * p.S + 2 * j + 1];
-            gam[(1 + k) * 32] = (h * Real(0.5)) * (c1[k] + c2[k]);
+            put(1 + k, (h * Real(0.5)) * (c1[k] + c2[k]));
         }
         wc = (Real)(1.7320508075688772 / 12.0) * h * h;
-        (void)w1;
-    } else {  // Simpson: c1 = start, c2 = end; centre sample only in Omega_1
+    } else {  // Simpson: c1 = slice start, c2 = slice end; the centre sample enters Omega_1 only
         for (int k = 0; k < K; ++k) {
             const Real a = c[(int64_t)k * p.S + 2 * j];
             const Real m = c[(int64_t)k * p.S + 2 * j + 1];
             const Real b = c[(int64_t)k * p.S + 2 * j + 2];
             c1[k] = a;
             c2[k] = b;
-            gam[(1 + k) * 32] = (h / Real(6)) * (a + Real(4) * m + b);
+            put(1 + k, (h / Real(6)) * (a + Real(4) * m + b));
         }
         wc = h * h / Real(12);
-        (void)w1;
     }
-    for (int k = 0; k < K; ++k) gam[(1 + K + k) * 32] = wc * (c2[k] - c1[k]);
+    for (int k = 0; k < K; ++k) put(1 + K + k, wc * (c2[k] - c1[k]));
     int e = 1 + 2 * K;
     for (int k = 0; k < K; ++k)
-        for (int l = k + 1; l < K; ++l, ++e) gam[e * 32] = wc * (c1[k] * c2[l] - c2[k] * c1[l]);
+        for (int l = k + 1; l < K; ++l, ++e) put(e, wc * (c1[k] * c2[l] - c2[k] * c1[l]));
 }
 
 // Class index for a norm bound: first class with cap >= nu (binary search in FP64).
@@ -158,19 +215,31 @@ __device__ __forceinline__ int find_class(const FusedParams &p, double nu, unsig
     return lo;
 }
 
+// 4 consecutive packed entries of a basis matrix
+template <typename Real> __device__ __forceinline__ void ld4(const Real *p, Real (&o)[4]);
+template <> __device__ __forceinline__ void ld4<float>(const float *p, float (&o)[4]) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+template <> __device__ __forceinline__ void ld4<double>(const double *p, double (&o)[4]) {
+    const double2 a = *reinterpret_cast<const double2 *>(p);
+    const double2 b = *reinterpret_cast<const double2 *>(p + 2);
+    o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
+}
+
 template <typename Real, int D, int INTEG>
-__global__ void __launch_bounds__(256) fused_small_kernel(const FusedParams p) {
-    using G = Geo<D>;
-    using C = typename Cx<Real>::T;
+__global__ void __launch_bounds__(256, 1) fused_small_kernel(const FusedParams p) {
+    using G = Geo<Real, D>;
+    using C = typename G::C;
     constexpr int LANES = G::LANES, GPW = G::GPW, TR = G::TR, TC = G::TC, LD = G::LD, DD = G::DD;
-    constexpr int SLOT = G::SLOT, NSLOT = G::NSLOT;
+    constexpr int SLOT = G::SLOT, NCH = G::NCH, PS = G::PS;
 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_second;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
     const int g = lane / LANES, gl = lane % LANES;
-    const int rb = gl / G::CBN, cb = gl % G::CBN;
+    const int rb = gl / G::CBW, cb = gl % G::CBW;
     const int nb = p.n_basis;
 
     Real *basis = (Real *)smem;
@@ -178,9 +247,9 @@ __global__ void __launch_bounds__(256) fused_small_kernel(const FusedParams p) {
     const size_t boff = basis_smem_bytes<Real, D>(nb);
     const size_t wsb = warp_ws_bytes<Real, D>(nb);
     unsigned char *wbase = smem + boff + (size_t)warp * wsb;
-    C *slots = (C *)wbase + (size_t)g * NSLOT * SLOT;
-    C *S1 = slots, *S2 = slots + SLOT, *S3 = slots + 2 * SLOT, *ST = slots + 3 * SLOT, *SR = slots + 4 * SLOT;
-    Real *gam = (Real *)(wbase + (size_t)GPW * NSLOT * SLOT * sizeof(C));
+    C *slots = (C *)(wbase + (size_t)g * G::GSTRIDE);
+    C *S1 = slots, *S2 = slots + SLOT, *S3 = slots + 2 * SLOT, *SR = slots + 3 * SLOT;
+    Real *gam = (Real *)(wbase + (size_t)GPW * G::GSTRIDE);
     int *cls = (int *)(gam + (size_t)nb * 32);
 
     // ---- basis and its norms into shared memory
@@ -204,7 +273,7 @@ __global__ void __launch_bounds__(256) fused_small_kernel(const FusedParams p) {
         for (int r = 0; r < TR; ++r)
 #pragma unroll
             for (int c = 0; c < TC; ++c)
-                t[r][c] = Cx<Real>::make((rb + r * G::RBN) == (cb + c * G::CBN) ? Real(1) : Real(0), Real(0));
+                t[r][c] = Cx<Real>::make((rb + r * G::RBN) == G::col(cb, c) ? Real(1) : Real(0), Real(0));
         st_tile<Real, D>(SR, rb, cb, t);
     }
     __syncthreads();
@@ -231,80 +300,64 @@ __global__ void __launch_bounds__(256) fused_small_kernel(const FusedParams p) {
             const int q = cls_q(code), rh = cls_r(code);
             const int s = cls_s(code) + p.extra_squarings;
 
-            // -- exponent: packed G = sum_e gamma_e P_e (lane's tile of the packed array)
-            Real gp[TR][TC];
-#pragma unroll
-            for (int r = 0; r < TR; ++r)
-#pragma unroll
-                for (int c = 0; c < TC; ++c) gp[r][c] = Real(0);
+            // -- exponent in packed form: lane owns chunks gl + LANES * t of 4 entries
+            Real *gpk = (Real *)S2;  // scratch until X^2 is formed
             {
+                Real acc[NCH][4];
+#pragma unroll
+                for (int t = 0; t < NCH; ++t)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) acc[t][u] = Real(0);
                 const Real *gcol = gam + g * LANES + rr;
                 for (int e = 0; e < nb; ++e) {
                     const Real ge = gcol[e * 32];
                     const Real *Pe = basis + e * DD;
 #pragma unroll
-                    for (int r = 0; r < TR; ++r)
+                    for (int t = 0; t < NCH; ++t) {
+                        Real v[4];
+                        ld4<Real>(Pe + 4 * (gl + LANES * t), v);
 #pragma unroll
-                        for (int c = 0; c < TC; ++c)
-                            gp[r][c] = fma(ge, Pe[(rb + r * G::RBN) * D + cb + c * G::CBN], gp[r][c]);
+                        for (int u = 0; u < 4; ++u) acc[t][u] = fma(ge, v[u], acc[t][u]);
+                    }
                 }
+#pragma unroll
+                for (int t = 0; t < NCH; ++t)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int pos = 4 * (gl + LANES * t) + u;
+                        gpk[(pos / D) * PS + (pos % D)] = acc[t][u];
+                    }
             }
-            Real *gpk = (Real *)ST;
-#pragma unroll
-            for (int r = 0; r < TR; ++r)
-#pragma unroll
-                for (int c = 0; c < TC; ++c) gpk[(rb + r * G::RBN) * D + cb + c * G::CBN] = gp[r][c];
             __syncwarp();
 
-            // -- unpack the Hermitian G into A = -i G / 2^s (row stride LD)
-            const Real sc = (Real)ldexp(1.0, -s);
-            C x1[TR][TC], x2[TR][TC], x3[TR][TC];
+            // -- unpack the Hermitian G into A = -i G / 2^s at the lane's tile
+            const Real sc = pow2neg<Real>(s);
+            C x1[TR][TC], x2[TR][TC], tt[TR][TC];
 #pragma unroll
             for (int r = 0; r < TR; ++r)
 #pragma unroll
                 for (int c = 0; c < TC; ++c) {
-                    const int i = rb + r * G::RBN, jj = cb + c * G::CBN;
-                    const Real re = (i <= jj) ? gpk[i * D + jj] : gpk[jj * D + i];
-                    const Real im = (i > jj) ? gpk[i * D + jj] : ((i < jj) ? -gpk[jj * D + i] : Real(0));
+                    const int i = rb + r * G::RBN, jj = G::col(cb, c);
+                    const Real a = gpk[i * PS + jj], b = gpk[jj * PS + i];
+                    const Real re = (i <= jj) ? a : b;
+                    const Real im = (i > jj) ? a : ((i < jj) ? -b : Real(0));
                     x1[r][c] = Cx<Real>::make(im * sc, -re * sc);
                 }
-            __syncwarp();
             st_tile<Real, D>(S1, rb, cb, x1);
             __syncwarp();
 
-            // -- powers X^2, X^3
-            if (q >= 2) {
-                mm_tile<Real, D>(S1, S1, rb, cb, x2);
-                st_tile<Real, D>(S2, rb, cb, x2);
-                __syncwarp();
-            }
-            if (q >= 3) {
-                mm_tile<Real, D>(S2, S1, rb, cb, x3);
-                st_tile<Real, D>(S3, rb, cb, x3);
-                __syncwarp();
-            }
+            // -- every complex product of the slice goes through one call site (one copy of
+            //    the unrolled product in the instruction stream):
+            //      X^2 (q >= 2), X^3 (q >= 3)           powers of X = A
+            //      T <- X^q T + B_b  (rh - 1 times)     Horner over blocks, with
+            //                                           T = a_{q rh} X^q + B_{rh-1} to start and
+            //                                           B_b = sum_{l<q} a_{q b + l} X^l
+            //      T <- T T          (s times)          squarings
+            //      R <- T R                             leaf product (later slice on the left)
+            const Real atop = coef<Real>(p, q * rh);
             const C *Sq = (q == 1) ? S1 : ((q == 2) ? S2 : S3);
-
-            // -- Horner over blocks: T = a_{q r} X^q + B_{r-1}; T = X^q T + B_b
-            //    with B_b = sum_{l<q} a_{q b + l} X^l
-            C tt[TR][TC];
-            {
-                const Real atop = coef<Real>(p, q * rh);
-#pragma unroll
-                for (int r = 0; r < TR; ++r)
-#pragma unroll
-                    for (int c = 0; c < TC; ++c) {
-                        const C xq = (q == 1) ? x1[r][c] : ((q == 2) ? x2[r][c] : x3[r][c]);
-                        tt[r][c] = Cx<Real>::make(atop * xq.x, atop * xq.y);
-                    }
-            }
-            for (int b = rh - 1; b >= 0; --b) {
-                if (b < rh - 1) {
-                    st_tile<Real, D>(ST, rb, cb, tt);
-                    __syncwarp();
-                    mm_tile<Real, D>(Sq, ST, rb, cb, tt);
-                    __syncwarp();
-                }
+            C *ST = (q == 1) ? S2 : S1;  // operand slot of Horner, squarings and the leaf product
+            auto add_block = [&](int b) {
                 const Real a0 = coef<Real>(p, q * b);
                 const Real a1 = (q >= 2) ? coef<Real>(p, q * b + 1) : Real(0);
                 const Real a2 = (q >= 3) ? coef<Real>(p, q * b + 2) : Real(0);
@@ -312,37 +365,76 @@ __global__ void __launch_bounds__(256) fused_small_kernel(const FusedParams p) {
                 for (int r = 0; r < TR; ++r)
 #pragma unroll
                     for (int c = 0; c < TC; ++c) {
-                        const bool diag = (rb + r * G::RBN) == (cb + c * G::CBN);
+                        const bool diag = (rb + r * G::RBN) == G::col(cb, c);
                         C v = tt[r][c];
-                        if (q == 1) {
-                            v.x = fma(a0, diag ? Real(1) : Real(0), v.x);
-                        } else {
-                            v.x = fma(a1, x1[r][c].x, v.x + (diag ? a0 : Real(0)));
+                        v.x += diag ? a0 : Real(0);
+                        if (q >= 2) {
+                            v.x = fma(a1, x1[r][c].x, v.x);
                             v.y = fma(a1, x1[r][c].y, v.y);
-                            if (q >= 3) {
-                                v.x = fma(a2, x2[r][c].x, v.x);
-                                v.y = fma(a2, x2[r][c].y, v.y);
-                            }
+                        }
+                        if (q >= 3) {
+                            v.x = fma(a2, x2[r][c].x, v.x);
+                            v.y = fma(a2, x2[r][c].y, v.y);
                         }
                         tt[r][c] = v;
                     }
-            }
-
-            // -- squarings
-            for (int i = 0; i < s; ++i) {
-                st_tile<Real, D>(ST, rb, cb, tt);
+            };
+            auto start_horner = [&](const C (&top)[TR][TC]) {
+#pragma unroll
+                for (int r = 0; r < TR; ++r)
+#pragma unroll
+                    for (int c = 0; c < TC; ++c) tt[r][c] = Cx<Real>::make(atop * top[r][c].x, atop * top[r][c].y);
+                add_block(rh - 1);
+            };
+            const int n_pow = q - 1, n_hor = rh - 1;
+            const int n_prod = n_pow + n_hor + s + 1;
+            int blk = rh - 1;
+            if (n_pow == 0) start_horner(x1);
+            for (int pi = 0; pi < n_prod; ++pi) {
+                const C *A, *B;
+                if (pi < n_pow) {
+                    A = (pi == 0) ? S1 : S2;
+                    B = S1;
+                } else {
+                    st_tile<Real, D>(ST, rb, cb, tt);
+                    __syncwarp();
+                    if (pi < n_pow + n_hor) {
+                        A = Sq;
+                        B = ST;
+                    } else {
+                        A = ST;
+                        B = (pi < n_prod - 1) ? ST : SR;
+                    }
+                }
+                C acc[TR][TC];
+                mm_tile<Real, D>(A, B, rb, cb, acc);
                 __syncwarp();
-                mm_tile<Real, D>(ST, ST, rb, cb, tt);
-                __syncwarp();
+                if (pi < n_pow) {
+                    if (pi == 0) {
+#pragma unroll
+                        for (int r = 0; r < TR; ++r)
+#pragma unroll
+                            for (int c = 0; c < TC; ++c) x2[r][c] = acc[r][c];
+                    }
+                    st_tile<Real, D>(pi == 0 ? S2 : S3, rb, cb, acc);
+                    if (pi == n_pow - 1) start_horner(acc);
+                    __syncwarp();
+                } else if (pi < n_pow + n_hor) {
+#pragma unroll
+                    for (int r = 0; r < TR; ++r)
+#pragma unroll
+                        for (int c = 0; c < TC; ++c) tt[r][c] = acc[r][c];
+                    add_block(--blk);
+                } else if (pi < n_prod - 1) {
+#pragma unroll
+                    for (int r = 0; r < TR; ++r)
+#pragma unroll
+                        for (int c = 0; c < TC; ++c) tt[r][c] = acc[r][c];
+                } else {
+                    st_tile<Real, D>(SR, rb, cb, acc);
+                    __syncwarp();
+                }
             }
-
-            // -- leaf product R <- U_j R
-            st_tile<Real, D>(ST, rb, cb, tt);
-            __syncwarp();
-            mm_tile<Real, D>(ST, SR, rb, cb, tt);
-            __syncwarp();
-            st_tile<Real, D>(SR, rb, cb, tt);
-            __syncwarp();
 
             if (gl == 0 && (t0 + rr) < len) {
                 n_exp += (unsigned long long)((q - 1) + (rh - 1) + s);
@@ -355,13 +447,11 @@ __global__ void __launch_bounds__(256) fused_small_kernel(const FusedParams p) {
     }
 
     // ---- statistics and status (before this block's tree arrival)
-    if (gl == 0) {
-        if (n_tree) {
-            atomicAdd(&p.counters[0], n_exp);
-            atomicAdd(&p.counters[1], n_tree);
-            atomicMax(&p.counters[2], (unsigned long long)m_max);
-            atomicMax(&p.counters[3], (unsigned long long)s_max);
-        }
+    if (gl == 0 && n_tree) {
+        atomicAdd(&p.counters[0], n_exp);
+        atomicAdd(&p.counters[1], n_tree);
+        atomicMax(&p.counters[2], (unsigned long long)m_max);
+        atomicMax(&p.counters[3], (unsigned long long)s_max);
     }
     if (flags) atomicOr(&p.status[0], flags);
 
@@ -370,7 +460,7 @@ __global__ void __launch_bounds__(256) fused_small_kernel(const FusedParams p) {
     const int n_leaf = W * GPW;
     const int gid = warp * GPW + g;  // block-wide group id
     auto leaf_R = [&](int l) -> C * {
-        return (C *)(smem + boff + (size_t)(l / GPW) * wsb) + (size_t)(l % GPW) * NSLOT * SLOT + 4 * SLOT;
+        return (C *)(smem + boff + (size_t)(l / GPW) * wsb + (size_t)(l % GPW) * G::GSTRIDE) + 3 * SLOT;
     };
     for (int h = 1; h < n_leaf; h <<= 1) {
         const int left = gid * 2 * h;
@@ -394,10 +484,11 @@ __global__ void __launch_bounds__(256) fused_small_kernel(const FusedParams p) {
     __threadfence();
     __syncthreads();
 
-    // ---- pairwise tree over blocks: second arrival at a node multiplies right * left
-    using GD = Geo<D>;
+    // ---- pairwise tree over blocks in FP64: second arrival at a node multiplies right * left
+    using GD = Geo<double, D>;
     double2 *bufL = (double2 *)(smem + boff);  // warp 0's workspace, free by now
-    double2 *bufR = bufL + D * LD;
+    double2 *bufR = bufL + D * GD::LD;
+    const int rb64 = (lane % GD::LANES) / GD::CBW, cb64 = (lane % GD::LANES) % GD::CBW;
     int idx = blockIdx.x, n = gridDim.x, level = 0, toff = 0;
     while (n > 1) {
         const int parent = idx >> 1;
@@ -410,19 +501,19 @@ __global__ void __launch_bounds__(256) fused_small_kernel(const FusedParams p) {
             const double2 *gL = p.partials + (size_t)((idx & ~1) << level) * DD;
             const double2 *gR = p.partials + (size_t)((idx | 1) << level) * DD;
             for (int t = tid; t < DD; t += blockDim.x) {
-                bufL[(t / D) * LD + t % D] = __ldcg(gL + t);
-                bufR[(t / D) * LD + t % D] = __ldcg(gR + t);
+                bufL[(t / D) * GD::LD + t % D] = __ldcg(gL + t);
+                bufR[(t / D) * GD::LD + t % D] = __ldcg(gR + t);
             }
             __syncthreads();
-            if (warp == 0 && g == 0) {
+            if (warp == 0 && lane < GD::LANES) {
                 double2 acc[GD::TR][GD::TC];
-                mm_tile<double, D>(bufR, bufL, rb, cb, acc);
+                mm_tile<double, D>(bufR, bufL, rb64, cb64, acc);
                 double2 *dst = p.partials + (size_t)((idx & ~1) << level) * DD;
 #pragma unroll
                 for (int r = 0; r < GD::TR; ++r)
 #pragma unroll
                     for (int c = 0; c < GD::TC; ++c)
-                        __stcg(dst + (rb + r * GD::RBN) * D + cb + c * GD::CBN, acc[r][c]);
+                        __stcg(dst + (rb64 + r * GD::RBN) * D + GD::col(cb64, c), acc[r][c]);
             }
             __threadfence();
             __syncthreads();
@@ -443,9 +534,7 @@ __global__ void __launch_bounds__(256) fused_small_kernel(const FusedParams p) {
         }
         if (tid == 0) {
             __threadfence();
-            for (int i = 0; i < 4; ++i) {
-                p.counters[4 + i] = atomicExch(&p.counters[i], 0ull);
-            }
+            for (int i = 0; i < 4; ++i) p.counters[4 + i] = atomicExch(&p.counters[i], 0ull);
             p.status[1] = atomicExch(&p.status[0], 0u);
         }
     }

@@ -32,6 +32,6 @@ size_t fused_smem_d16(int fp64, int n_basis, int warps) {
     return fp64 ? fused_smem_bytes<double, 16>(n_basis, warps) : fused_smem_bytes<float, 16>(n_basis, warps);
 }
 
-int fused_groups_per_warp_d16() { return Geo<16>::GPW; }
+int fused_groups_per_warp_d16(int fp64) { return fp64 ? Geo<double, 16>::GPW : Geo<float, 16>::GPW; }
 
 }  // namespace pm

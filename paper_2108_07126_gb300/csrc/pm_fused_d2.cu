@@ -32,6 +32,6 @@ size_t fused_smem_d2(int fp64, int n_basis, int warps) {
     return fp64 ? fused_smem_bytes<double, 2>(n_basis, warps) : fused_smem_bytes<float, 2>(n_basis, warps);
 }
 
-int fused_groups_per_warp_d2() { return Geo<2>::GPW; }
+int fused_groups_per_warp_d2(int fp64) { return fp64 ? Geo<double, 2>::GPW : Geo<float, 2>::GPW; }
 
 }  // namespace pm

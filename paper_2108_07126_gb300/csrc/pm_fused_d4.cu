@@ -32,6 +32,6 @@ size_t fused_smem_d4(int fp64, int n_basis, int warps) {
     return fp64 ? fused_smem_bytes<double, 4>(n_basis, warps) : fused_smem_bytes<float, 4>(n_basis, warps);
 }
 
-int fused_groups_per_warp_d4() { return Geo<4>::GPW; }
+int fused_groups_per_warp_d4(int fp64) { return fp64 ? Geo<double, 4>::GPW : Geo<float, 4>::GPW; }
 
 }  // namespace pm

@@ -32,6 +32,6 @@ size_t fused_smem_d8(int fp64, int n_basis, int warps) {
     return fp64 ? fused_smem_bytes<double, 8>(n_basis, warps) : fused_smem_bytes<float, 8>(n_basis, warps);
 }
 
-int fused_groups_per_warp_d8() { return Geo<8>::GPW; }
+int fused_groups_per_warp_d8(int fp64) { return fp64 ? Geo<double, 8>::GPW : Geo<float, 8>::GPW; }
 
 }  // namespace pm

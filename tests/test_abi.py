@@ -87,3 +87,48 @@ def test_taylor_theta_invalid():
 
     assert b.parament_taylor_theta(0, 1e-16) < 0
     assert b.parament_taylor_theta(3, 0.0) < 0
+
+
+PS_PRODUCTS = {1: 0, 2: 1, 4: 2, 6: 3, 9: 4, 12: 5}
+
+
+def brute_choice(nu, u, force_m=0):
+    """Cheapest (m, s) with nu / 2^s <= theta_m(u / 2^s), by enumeration in 50-digit arithmetic."""
+    import mpmath
+
+    mpmath.mp.dps = 50
+    best = None
+    for s in range(0, 63):
+        for m, cost in PS_PRODUCTS.items():
+            if force_m and m != force_m:
+                continue
+            x = mpmath.mpf(nu) / mpmath.mpf(2) ** s
+            ok = x == 0 or (m + 1) * mpmath.log(x) - mpmath.log(mpmath.factorial(m + 1)) + x <= mpmath.log(
+                mpmath.mpf(u) / mpmath.mpf(2) ** s)
+            if ok and (best is None or cost + s < best[0]):
+                best = (cost + s, m, s)
+    return best[1], best[2]
+
+
+@pytest.mark.parametrize("nu", [0.0, 1e-12, 1e-5, 0.01, 0.13, 0.16, 0.4, 1.0, 3.9, 12.0, 250.0])
+@pytest.mark.parametrize("u", [2.0 ** -53, 2.0 ** -24])
+def test_taylor_choice_is_cheapest_admissible(nu, u):
+    from paper_2108_07126_gb300 import binding as b
+
+    m, s = b.parament_taylor_choice(nu, u)
+    bm, bs = brute_choice(nu, u)
+    assert PS_PRODUCTS[m] + s == PS_PRODUCTS[bm] + bs
+    # admissible: the bound holds at the chosen pair
+    assert nu / 2 ** s <= b.parament_taylor_theta(m, u / 2 ** s) * (1 + 1e-12)
+
+
+def test_taylor_choice_forced_and_invalid():
+    from paper_2108_07126_gb300 import binding as b
+
+    for m in (4, 6, 9, 12):
+        mm, s = b.parament_taylor_choice(0.5, 2.0 ** -53, m)
+        assert mm == m and (m, s) == brute_choice(0.5, 2.0 ** -53, m)
+    with pytest.raises(b.ParamentError):
+        b.parament_taylor_choice(0.5, 2.0 ** -53, 5)
+    with pytest.raises(b.ParamentError):
+        b.parament_taylor_choice(float("nan"), 2.0 ** -53)

@@ -108,6 +108,27 @@ def test_empty_run_is_identity(prop):
         assert np.array_equal(U, np.eye(5))
 
 
+def test_zero_basis_matrices_are_dropped(prop):
+    """Controls on different qubits commute: their commutator basis matrices are zero and skipped."""
+    d = 8
+    Hk = np.stack([wl.embed(wl.SX, i, 3) for i in range(3)] + [wl.embed(wl.SY, 0, 3)])
+    rng = np.random.default_rng(17)
+    H0 = sum(rng.uniform(0.5, 1.5) * wl.embed(wl.SZ, i, 3) for i in range(3))
+    c = rng.standard_normal((4, 2 * 300))
+    prob = wl.Problem("commuting", H0, Hk, c, 0.05, "magnus4_gl2", 300)
+    U = run(prop, prob, "fp64")
+    assert np.max(np.abs(U - ref(prob))) <= TOL64
+    # 1 + 4 + 4 + 6 coefficients; the sx_i commute with each other and sy_0 commutes with sx_1, sx_2
+    assert prop.stats()["n_basis"] == 1 + 4 + 4 + 1
+
+
+def test_all_zero_hamiltonian(prop):
+    prob = wl.Problem("zero", np.zeros((3, 3), np.complex128), np.zeros((2, 3, 3), np.complex128),
+                      np.ones((2, 9)), 0.1, "magnus4_simpson", 4)
+    for prec in ("fp64", "fp32"):
+        assert np.array_equal(run(prop, prob, prec), np.eye(3))
+
+
 def test_drift_only_is_exact_exponential(prop):
     import scipy.linalg
 
@@ -141,11 +162,12 @@ def test_deterministic(prop):
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("m", [1, 2, 4, 6, 9, 12])
-def test_forced_taylor_degree(prop, m):
+@pytest.mark.parametrize("m,g_norm", [(1, 1e-9), (2, 1e-6), (4, 0.05), (6, 0.5), (9, 0.5), (12, 0.5)])
+def test_forced_taylor_degree(prop, m, g_norm):
+    """Forced degrees; low degrees only on small exponents (s squarings amplify rounding by 2^s)."""
     from paper_2108_07126_gb300 import binding as b
 
-    prob = wl.random_problem(8, 2, 50, "midpoint", seed=13, g_norm=0.5)
+    prob = wl.random_problem(8, 2, 50, "midpoint", seed=13, g_norm=g_norm)
     prop.set_option(b.PARAMENT_OPT_TAYLOR_DEGREE, m)
     U = run(prop, prob, "fp64")
     assert np.max(np.abs(U - ref(prob))) <= TOL64
