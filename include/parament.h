@@ -214,6 +214,45 @@ double parament_taylor_theta(int m, double u);
  */
 int parament_taylor_choice(double norm_bound, double u, int force_m, int *m_out, int *s_out);
 
+/*
+ * --- Propagation without allocation -----------------------------------------
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * cannot allocate device memory: an application or framework that owns all
+ * device memory through its own allocator, or a latency-critical loop that
+ * cannot afford the device-wide synchronisation of cudaMalloc / cudaFree.
+ *
+ * One call does what set_hamiltonians + set_controls + propagate do, without a
+ * context and without allocating anything (no cudaMalloc, cudaFree or
+ * allocating library routine).  Its intermediates live in one static device
+ * array of PARAMENT_NOALLOC_SCRATCH_BYTES bytes (about 1.6 MiB) that every GPU
+ * which loads the library holds until the process exits.
+ *   - H0 (d x d), Hk (K x d x d), c (K x S), U_out (d x d): device pointers,
+ *     layouts and S as for the context API; `dtype` for H and U, `cdtype` must
+ *     match `prec` (F64 with FP64, F32 with FP32).  The caller owns them all.
+ *   - Limits: d <= PARAMENT_NOALLOC_MAX_DIM, 1 + K (midpoint) or
+ *     1 + K (K + 3) / 2 (Magnus) <= PARAMENT_NOALLOC_MAX_BASIS, at most
+ *     PARAMENT_NOALLOC_MAX_BLOCKS thread blocks.  Beyond a limit: UNSUPPORTED;
+ *     host pointers, mismatched dtypes, bad sizes: INVALID_VALUE.
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address (cudaGetSymbolAddress); make that first call
+ *     before any stream capture.
+ *   - Every call shares the array, which keeps the latest call's contents
+ *     (the arrival counters are cleared by each call).  Calls whose work
+ *     overlaps on the GPU -- on two streams, or from two host threads -- race
+ *     on it and corrupt each other's results: keep them on one stream.
+ *   - Unlike set_hamiltonians it neither checks Hermiticity nor drops
+ *     identically zero basis matrices; U equals parament_propagate's up to
+ *     rounding.  Work is enqueued on cuda_stream (NULL = legacy default
+ *     stream); the call returns without waiting.
+ */
+#define PARAMENT_NOALLOC_MAX_DIM 16
+#define PARAMENT_NOALLOC_MAX_BASIS 45
+#define PARAMENT_NOALLOC_MAX_BLOCKS 304
+#define PARAMENT_NOALLOC_SCRATCH_BYTES 1641472
+int parament_propagate_noalloc(int dim, int n_ctrl, const void *H0, const void *Hk, parament_dtype dtype,
+                               parament_integrator integrator, const void *c, parament_real_dtype cdtype,
+                               int64_t n_steps, double dt, void *U_out, parament_precision prec, void *cuda_stream);
+
 /* Static text for a status code. */
 const char *parament_status_string(int status);
 

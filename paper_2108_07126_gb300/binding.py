@@ -104,6 +104,9 @@ _SIGS = {
     "parament_taylor_theta": ([ctypes.c_int, ctypes.c_double], ctypes.c_double),
     "parament_taylor_choice": ([ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "parament_propagate_noalloc": ([ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp,
+                                    ctypes.c_int, ctypes.c_int64, ctypes.c_double, _vp, ctypes.c_int, _vp],
+                                   ctypes.c_int),
     "parament_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "parament_last_error": ([_vp], ctypes.c_char_p),
 }
@@ -191,6 +194,15 @@ def parament_taylor_choice(norm_bound: float, u: float, force_m: int = 0) -> tup
     s = ctypes.c_int()
     _check(_lib.parament_taylor_choice(float(norm_bound), float(u), int(force_m), ctypes.byref(m), ctypes.byref(s)))
     return m.value, s.value
+
+
+def parament_propagate_noalloc(dim: int, n_ctrl: int, H0_ptr: int, Hk_ptr: int | None, dtype: int, integrator: int,
+                               c_ptr: int | None, cdtype: int, n_steps: int, dt: float, U_ptr: int, prec: int,
+                               stream: int | None = None) -> None:
+    """One propagation that allocates nothing (device pointers only; see parament.h)."""
+    _check(_lib.parament_propagate_noalloc(int(dim), int(n_ctrl), H0_ptr, Hk_ptr or None, int(dtype),
+                                           int(integrator), c_ptr or None, int(cdtype), int(n_steps), float(dt),
+                                           U_ptr, int(prec), stream or None))
 
 
 def raw_call(name: str, *args) -> int:

@@ -25,6 +25,7 @@ SOURCES = [
     "pm_fused_d4.cu",
     "pm_fused_d8.cu",
     "pm_fused_d16.cu",
+    "pm_noalloc.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -40,7 +41,7 @@ def nvcc() -> str:
 
 def _deps() -> list[str]:
     out = [os.path.join(INCLUDE, "parament.h")]
-    out += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
+    out += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     return out
 
 

@@ -785,3 +785,38 @@ int parament_get_option(const parament_ctx *ctx, int key, int64_t *value) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ helpers for other translation units
+
+#include "pm_internal.h"
+
+namespace pm {
+
+int fill_classes(double u, int force_m, FusedParams &p) { return build_classes(u, force_m, p); }
+
+cudaError_t fused_launch(int Dp, int fp64, int integ, const FusedParams &p, int grid, int warps, size_t smem,
+                         cudaStream_t st) {
+    return fused_dispatch(Dp, fp64, integ, p, grid, warps, smem, st);
+}
+
+int fused_occupancy(int Dp, int fp64, int integ, int warps, size_t smem) {
+    return fused_blocks_per_sm(Dp, fp64, integ, warps, smem);
+}
+
+size_t fused_smem_size(int Dp, int fp64, int n_basis, int warps) { return fused_smem(Dp, fp64, n_basis, warps); }
+
+int fused_groups(int Dp, int fp64) { return fused_gpw(Dp, fp64); }
+
+cudaError_t basis_build(const void *raw, int c128, int d, int Dp, int K, int magnus, int nb, double2 *full,
+                        double *p64, float *p32, double *bnorm, double *bmax, cudaStream_t st) {
+    if (c128)
+        build_basis_kernel<double2><<<nb, 256, 0, st>>>((const double2 *)raw, d, Dp, K, magnus, full);
+    else
+        build_basis_kernel<float2><<<nb, 256, 0, st>>>((const float2 *)raw, d, Dp, K, magnus, full);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    pack_basis_kernel<<<nb, 256, 0, st>>>(full, Dp, p64, p32, bnorm, bmax);
+    return cudaGetLastError();
+}
+
+}  // namespace pm
