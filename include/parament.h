@@ -108,7 +108,12 @@ typedef enum {
     /* extra squarings added to every slice (default 0; accuracy experiments) */
     PARAMENT_OPT_EXTRA_SQUARINGS = 5,
     /* Hermiticity tolerance in units of 1e-12 relative to max |H_ab| (default 1000, i.e. 1e-9) */
-    PARAMENT_OPT_HERMITIAN_TOL_E12 = 7
+    PARAMENT_OPT_HERMITIAN_TOL_E12 = 7,
+    /* gradient: slices per sub-chunk of the adjoint sweep (0 = auto: a whole leaf when it fits the
+       workspace cap); leaves longer than a sub-chunk are re-computed from checkpoints */
+    PARAMENT_OPT_GRAD_SUBCHUNK = 8,
+    /* gradient: cap in MiB on the per-slice prefix buffer of the adjoint sweep (default 4096) */
+    PARAMENT_OPT_WORKSPACE_MB = 9
 } parament_option;
 
 /* per-call diagnostics of the most recent propagate (see parament_get_stats) */
@@ -121,7 +126,7 @@ typedef struct {
     int32_t leaves;           /* sequential leaf products below the pairwise tree */
     int32_t max_degree;       /* largest Taylor degree used */
     int32_t max_squarings;    /* largest number of squarings used */
-    int32_t reserved0;
+    int32_t grad_subchunk;    /* slices per sub-chunk of the latest gradient (0 if none) */
     int64_t exp_products;     /* complex d x d products in exponentials and squarings */
     int64_t tree_products;    /* complex d x d products in the product tree */
     uint32_t device_status;   /* PARAMENT_DEV_* bits raised by the kernels */
@@ -186,6 +191,23 @@ int parament_set_controls(parament_ctx *ctx, const void *c, parament_real_dtype 
  * Requires set_hamiltonians and set_controls.
  */
 int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec);
+
+/*
+ * Gate-fidelity loss and its gradient with respect to every control sample
+ * (midpoint rule; Sec. 7 names GRAPE-type optimal control as the application,
+ * the paper gives no gradient formula).  With z = Tr(V^dagger U(T)):
+ *   *loss_out = 1 - |z|^2 / d^2                         (host double; NULL = skip, no wait)
+ *   grad_out[k * N + j] = dL / dc_k(t_j)                (K x N; double for FP64, float for FP32)
+ * U = S_j U_j P_{j-1}; dz/dc_kj = Tr(L_{X_j}(P_{j-1} V^dagger S_j) (-i dt H_k)) with X_j = -i G_j and
+ * L_X the Frechet derivative of exp, taken as the upper-right block of exp([[X, Lambda], [0, X]]).
+ * The prefixes P and suffixes S come from the forward tree: leaf and block products of the forward
+ * kernel, exclusive scans over them, then per leaf a forward sweep (prefixes, re-computed from
+ * checkpoints for long leaves) and a backward sweep.  V: d x d in the dtype of set_hamiltonians;
+ * U_out: optional U(T).  Pointers host or device.  Errors: UNSUPPORTED for the Magnus integrators
+ * and tensor-core precisions; STATE before set_controls.
+ */
+int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, void *grad_out, void *U_out,
+                            parament_precision prec);
 
 /* Diagnostics of the latest propagate; waits for the stream. */
 int parament_get_stats(parament_ctx *ctx, parament_stats *out);

@@ -56,6 +56,8 @@ PARAMENT_OPT_BLOCK_WARPS = 3
 PARAMENT_OPT_CHECK_HERMITIAN = 4
 PARAMENT_OPT_EXTRA_SQUARINGS = 5
 PARAMENT_OPT_HERMITIAN_TOL_E12 = 7
+PARAMENT_OPT_GRAD_SUBCHUNK = 8
+PARAMENT_OPT_WORKSPACE_MB = 9
 
 PARAMENT_DEV_NONFINITE_NORM = 0x1
 PARAMENT_DEV_NORM_CAPPED = 0x2
@@ -76,7 +78,7 @@ class parament_stats(ctypes.Structure):
         ("leaves", ctypes.c_int32),
         ("max_degree", ctypes.c_int32),
         ("max_squarings", ctypes.c_int32),
-        ("reserved0", ctypes.c_int32),
+        ("grad_subchunk", ctypes.c_int32),
         ("exp_products", ctypes.c_int64),
         ("tree_products", ctypes.c_int64),
         ("device_status", ctypes.c_uint32),
@@ -98,6 +100,7 @@ _SIGS = {
                                   ctypes.c_int),
     "parament_set_controls": ([_vp, _vp, ctypes.c_int, ctypes.c_int64, ctypes.c_double], ctypes.c_int),
     "parament_propagate": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
+    "parament_propagate_grad": ([_vp, _vp, ctypes.POINTER(ctypes.c_double), _vp, _vp, ctypes.c_int], ctypes.c_int),
     "parament_get_stats": ([_vp, ctypes.POINTER(parament_stats)], ctypes.c_int),
     "parament_set_option": ([_vp, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
     "parament_get_option": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -167,6 +170,14 @@ def parament_set_controls(ctx, c_ptr: int | None, cdtype: int, n_steps: int, dt:
 
 def parament_propagate(ctx, U_ptr: int, prec: int) -> None:
     _check(_lib.parament_propagate(ctx, U_ptr, int(prec)), ctx)
+
+
+def parament_propagate_grad(ctx, V_ptr: int, grad_ptr: int, U_ptr: int | None, prec: int,
+                            want_loss: bool = True) -> float | None:
+    loss = ctypes.c_double(float("nan"))
+    _check(_lib.parament_propagate_grad(ctx, V_ptr, ctypes.byref(loss) if want_loss else None, grad_ptr,
+                                        U_ptr or None, int(prec)), ctx)
+    return loss.value if want_loss else None
 
 
 def parament_get_stats(ctx) -> dict:
@@ -289,6 +300,18 @@ class Propagator:
         self._sync_stream()
         parament_propagate(self.ctx, out.data_ptr(), PRECISIONS[prec])
         return out
+
+    def propagate_grad(self, V, prec: str = "fp64", want_U: bool = False):
+        """Loss 1 - |Tr(V^dagger U)|^2 / d^2, its gradient (K, N) w.r.t. the controls, optionally U."""
+        torch = self._torch
+        V = torch.as_tensor(V).to(self.dtype).to(self.device).contiguous()
+        rdt = torch.float64 if prec == "fp64" else torch.float32
+        grad = torch.empty(self.n_ctrl, self.n_steps, dtype=rdt, device=self.device)
+        U = torch.empty(self.dim, self.dim, dtype=self.dtype, device=self.device) if want_U else None
+        self._sync_stream()
+        loss = parament_propagate_grad(self.ctx, V.data_ptr(), grad.data_ptr(), U.data_ptr() if want_U else None,
+                                       PRECISIONS[prec])
+        return (loss, grad, U) if want_U else (loss, grad)
 
     def stats(self) -> dict:
         return parament_get_stats(self.ctx)

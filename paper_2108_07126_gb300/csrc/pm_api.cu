@@ -13,13 +13,17 @@
 
 #include "../../include/parament.h"
 #include "pm_common.cuh"
+#include "pm_grad.cuh"
 
 namespace pm {
 #define PM_DECL_D(D)                                                                                     \
     cudaError_t fused_dispatch_d##D(int, int, const FusedParams &, int, int, size_t, cudaStream_t);      \
     int fused_blocks_per_sm_d##D(int, int, int, size_t);                                                 \
     size_t fused_smem_d##D(int, int, int);                                                               \
-    int fused_groups_per_warp_d##D(int);
+    int fused_groups_per_warp_d##D(int);                                                                 \
+    cudaError_t grad_run_d##D(int, const ScanParams &, const GradParams &, int, int, size_t, cudaStream_t); \
+    int adjoint_blocks_per_sm_d##D(int, int, size_t);                                                     \
+    size_t adjoint_smem_d##D(int, int, int);
 PM_DECL_D(2)
 PM_DECL_D(4)
 PM_DECL_D(8)
@@ -55,6 +59,7 @@ struct parament_ctx {
 
     Workspace hraw, full, packed64, packed32, bnorm, partials, tickets, counters, status, check;
     Workspace ctrl_copy, ctrl_conv, uout, bmax, cpacked64, cpacked32, cbnorm;
+    Workspace gv, gvdag, gleaf, gblock, gbpin, gpin, gz, gpbuf, gckpt, ggrad;
     int nb_eff = 0;
     std::vector<short> slot_of;
 
@@ -64,6 +69,7 @@ struct parament_ctx {
     double dt = 0.0;
 
     int64_t opt_degree = 0, opt_grid = 0, opt_warps = 0, opt_check_herm = 1, opt_extra_sq = 0, opt_herm_tol = 1000;
+    int64_t opt_grad_subchunk = 0, opt_workspace_mb = 4096;
 
     parament_stats last{};
     std::string err;
@@ -282,15 +288,18 @@ struct Cand {
 
 const int kDegrees[][3] = {{1, 1, 1}, {2, 2, 1}, {4, 2, 2}, {6, 3, 2}, {9, 3, 3}, {12, 3, 4}};  // m, q, r
 
-int build_classes(double u, int force_m, FusedParams &p) {
+// shift = 0: truncation bound of exp; shift = 1: of its Frechet derivative
+// (the derivative series loses one power: remainder ~ x^m / m! e^x).
+int build_classes(double u, int force_m, FusedParams &p, int shift = 0) {
     std::vector<Cand> all;
     for (int s = 0; s <= 62; ++s) {
         for (const auto &dg : kDegrees) {
             const int m = dg[0], q = dg[1], r = dg[2];
             if (force_m > 0 && m != force_m) continue;
+            if (m - shift < 1) continue;
             // s squarings multiply the truncation error of exp(A / 2^s) by 2^s: the
             // polynomial must meet u / 2^s so that the squared result meets u.
-            const double th = parament_taylor_theta(m, std::ldexp(u, -s));
+            const double th = parament_taylor_theta(m - shift, std::ldexp(u, -s));
             if (!(th > 0.0)) continue;
             all.push_back({std::ldexp(th, s), (q - 1) + (r - 1) + s, m, q, r, s});
         }
@@ -347,6 +356,34 @@ size_t fused_smem(int Dp, int fp64, int nb, int warps) {
         case 4: return fused_smem_d4(fp64, nb, warps);
         case 8: return fused_smem_d8(fp64, nb, warps);
         case 16: return fused_smem_d16(fp64, nb, warps);
+    }
+    return 0;
+}
+cudaError_t grad_run(int Dp, int fp64, const ScanParams &sp, const GradParams &gp, int grid, int warps, size_t smem,
+                     cudaStream_t st) {
+    switch (Dp) {
+        case 2: return grad_run_d2(fp64, sp, gp, grid, warps, smem, st);
+        case 4: return grad_run_d4(fp64, sp, gp, grid, warps, smem, st);
+        case 8: return grad_run_d8(fp64, sp, gp, grid, warps, smem, st);
+        case 16: return grad_run_d16(fp64, sp, gp, grid, warps, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+int adjoint_blocks_per_sm(int Dp, int fp64, int warps, size_t smem) {
+    switch (Dp) {
+        case 2: return adjoint_blocks_per_sm_d2(fp64, warps, smem);
+        case 4: return adjoint_blocks_per_sm_d4(fp64, warps, smem);
+        case 8: return adjoint_blocks_per_sm_d8(fp64, warps, smem);
+        case 16: return adjoint_blocks_per_sm_d16(fp64, warps, smem);
+    }
+    return 0;
+}
+size_t adjoint_smem(int Dp, int fp64, int K, int warps) {
+    switch (Dp) {
+        case 2: return adjoint_smem_d2(fp64, K, warps);
+        case 4: return adjoint_smem_d4(fp64, K, warps);
+        case 8: return adjoint_smem_d8(fp64, K, warps);
+        case 16: return adjoint_smem_d16(fp64, K, warps);
     }
     return 0;
 }
@@ -466,7 +503,8 @@ int parament_destroy(parament_ctx *ctx) {
         Workspace *all[] = {&ctx->hraw, &ctx->full, &ctx->packed64, &ctx->packed32, &ctx->bnorm,
                             &ctx->partials, &ctx->tickets, &ctx->counters, &ctx->status, &ctx->check,
                             &ctx->ctrl_copy, &ctx->ctrl_conv, &ctx->uout, &ctx->bmax, &ctx->cpacked64,
-                            &ctx->cpacked32, &ctx->cbnorm};
+                            &ctx->cpacked32, &ctx->cbnorm, &ctx->gv, &ctx->gvdag, &ctx->gleaf, &ctx->gblock,
+                            &ctx->gbpin, &ctx->gpin, &ctx->gz, &ctx->gpbuf, &ctx->gckpt, &ctx->ggrad};
         for (Workspace *w : all) ws_free(*w);
     }
     delete ctx;
@@ -613,20 +651,15 @@ int parament_set_controls(parament_ctx *ctx, const void *c, parament_real_dtype 
     return PARAMENT_OK;
 }
 
-int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) {
-    if (!ctx) return PARAMENT_ERR_INVALID_VALUE;
-    ctx->err.clear();
-    if (ctx->state < 2) return set_err(ctx, PARAMENT_ERR_STATE, "set_hamiltonians and set_controls must come first");
-    if (!U_out) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "null U_out");
-    if (prec == PARAMENT_PREC_FP32_TC_BF16X3 || prec == PARAMENT_PREC_FP32_TC_TF32X3)
-        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "tensor-core precision modes need d >= 32; not in this build");
-    if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32)
-        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown precision %d", (int)prec);
-    DeviceGuard guard(ctx->device);
-    const int fp64 = prec == PARAMENT_PREC_FP64;
-    const int Dp = ctx->dpad, nb = ctx->nb_eff;
+}  // extern "C"
 
-    // controls in the compute type
+namespace {
+
+// Controls in the compute type, Taylor table and launch geometry of the fused
+// forward kernel (shared by propagate and propagate_grad).
+int forward_setup(parament_ctx *ctx, int fp64, void *U_dst, FusedParams &p, int &grid, int &warps, size_t &smem,
+                  int &leaves_per_block) {
+    const int Dp = ctx->dpad, nb = ctx->nb_eff;
     const void *ctrl = ctx->ctrl;
     const int64_t count = (int64_t)ctx->K * ctx->S;
     const bool want64 = fp64 != 0;
@@ -644,45 +677,32 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) 
         ctrl = ctx->ctrl_conv.ptr;
     }
 
-    FusedParams p;
     std::memset(&p, 0, sizeof(p));
     const double u = fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
     if (build_classes(u, (int)ctx->opt_degree, p) <= 0)
         return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "Taylor degree %lld is not one of 1, 2, 4, 6, 9, 12",
                        (long long)ctx->opt_degree);
 
-    // launch geometry
-    int warps = (int)ctx->opt_warps;
+    warps = (int)ctx->opt_warps;
     if (warps <= 0) {
         warps = 8;
         while (warps > 1 && fused_smem(Dp, fp64, nb, warps) > ctx->smem_optin) --warps;
     }
     if (warps > 8) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "at most 8 warps per block");
-    const size_t smem = fused_smem(Dp, fp64, nb, warps);
+    smem = fused_smem(Dp, fp64, nb, warps);
     if (smem > ctx->smem_optin)
         return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "basis of %d matrices (d=%d) needs %zu B shared memory > %zu",
                        nb, ctx->dim, smem, ctx->smem_optin);
     const int bps = fused_blocks_per_sm(Dp, fp64, (int)ctx->integ, warps, smem);
     if (bps <= 0) return set_err(ctx, PARAMENT_ERR_CUDA, "occupancy query failed (%d warps, %zu B)", warps, smem);
-    const int leaves_per_block = warps * fused_gpw(Dp, fp64);
-    int grid = (int)ctx->opt_grid;
+    leaves_per_block = warps * fused_gpw(Dp, fp64);
+    grid = (int)ctx->opt_grid;
     if (grid <= 0) {
         const int64_t need = (ctx->n_steps + (int64_t)leaves_per_block * kLeafMinSteps - 1) /
                              ((int64_t)leaves_per_block * kLeafMinSteps);
         grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)bps * ctx->sm_count));
     }
     grid = std::min(grid, ctx->max_grid);
-
-    const size_t esz = ctx->dtype == PARAMENT_C128 ? 16 : 8;
-    const bool host_out = !is_device_ptr(U_out);
-    void *dst = U_out;
-    if (host_out) {
-        int st = ws_reserve(ctx, ctx->uout, (size_t)ctx->dim * ctx->dim * esz);
-        if (st) return st;
-        dst = ctx->uout.ptr;
-    } else if ((uintptr_t)U_out % esz) {
-        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "U_out not aligned to its element size");
-    }
 
     p.ctrl = ctrl;
     p.S = ctx->S;
@@ -698,13 +718,14 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) 
     p.bnorm1 = (const double *)ctx->cbnorm.ptr;
     p.partials = (double2 *)ctx->partials.ptr;
     p.tickets = (unsigned *)ctx->tickets.ptr;
-    p.U_out = dst;
+    p.U_out = U_dst;
     p.counters = (unsigned long long *)ctx->counters.ptr;
     p.status = (unsigned *)ctx->status.ptr;
     p.extra_squarings = (int)ctx->opt_extra_sq;
+    return PARAMENT_OK;
+}
 
-    PM_CUDA(fused_dispatch(Dp, fp64, (int)ctx->integ, p, grid, warps, smem, ctx->stream));
-
+void record_launch(parament_ctx *ctx, int nb, int grid, int warps, int leaves_per_block) {
     ctx->last = parament_stats{};
     ctx->last.n_steps = ctx->n_steps;
     ctx->last.dim = ctx->dim;
@@ -713,9 +734,207 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) 
     ctx->last.block_threads = warps * 32;
     ctx->last.leaves = grid * leaves_per_block;
     ctx->last.kernel_ms = -1.0;
+}
+
+// V^dagger, padded with zeros to Dp x Dp, in FP64
+template <typename InT>
+__global__ void vdag_kernel(const InT *V, int d, int Dp, double2 *out) {
+    for (int t = threadIdx.x; t < Dp * Dp; t += blockDim.x) {
+        const int i = t / Dp, j = t % Dp;
+        double2 v = make_double2(0.0, 0.0);
+        if (i < d && j < d) {
+            const InT x = V[j * d + i];
+            v = make_double2((double)x.x, -(double)x.y);
+        }
+        out[t] = v;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) {
+    if (!ctx) return PARAMENT_ERR_INVALID_VALUE;
+    ctx->err.clear();
+    if (ctx->state < 2) return set_err(ctx, PARAMENT_ERR_STATE, "set_hamiltonians and set_controls must come first");
+    if (!U_out) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "null U_out");
+    if (prec == PARAMENT_PREC_FP32_TC_BF16X3 || prec == PARAMENT_PREC_FP32_TC_TF32X3)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "tensor-core precision modes need d >= 32; not in this build");
+    if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32)
+        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown precision %d", (int)prec);
+    DeviceGuard guard(ctx->device);
+    const int fp64 = prec == PARAMENT_PREC_FP64;
+
+    const size_t esz = ctx->dtype == PARAMENT_C128 ? 16 : 8;
+    const bool host_out = !is_device_ptr(U_out);
+    void *dst = U_out;
+    if (host_out) {
+        int st = ws_reserve(ctx, ctx->uout, (size_t)ctx->dim * ctx->dim * esz);
+        if (st) return st;
+        dst = ctx->uout.ptr;
+    } else if ((uintptr_t)U_out % esz) {
+        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "U_out not aligned to its element size");
+    }
+
+    FusedParams p;
+    int grid = 0, warps = 0, lpb = 0;
+    size_t smem = 0;
+    int st = forward_setup(ctx, fp64, dst, p, grid, warps, smem, lpb);
+    if (st) return st;
+    PM_CUDA(fused_dispatch(ctx->dpad, fp64, (int)ctx->integ, p, grid, warps, smem, ctx->stream));
+    record_launch(ctx, ctx->nb_eff, grid, warps, lpb);
 
     if (host_out) {
         PM_CUDA(cudaMemcpyAsync(U_out, dst, (size_t)ctx->dim * ctx->dim * esz, cudaMemcpyDeviceToHost, ctx->stream));
+        PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return PARAMENT_OK;
+}
+
+int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, void *grad_out, void *U_out,
+                            parament_precision prec) {
+    if (!ctx) return PARAMENT_ERR_INVALID_VALUE;
+    ctx->err.clear();
+    if (ctx->state < 2) return set_err(ctx, PARAMENT_ERR_STATE, "set_hamiltonians and set_controls must come first");
+    if (!V || !grad_out) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "null V or grad_out");
+    if (ctx->integ != PARAMENT_MIDPOINT)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "the adjoint gradient covers the midpoint rule");
+    if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "gradient precision must be FP64 or FP32");
+    DeviceGuard guard(ctx->device);
+    const int fp64 = prec == PARAMENT_PREC_FP64;
+    const int Dp = ctx->dpad, d = ctx->dim, K = ctx->K;
+    const size_t DD = (size_t)Dp * Dp;
+    const size_t esz = ctx->dtype == PARAMENT_C128 ? 16 : 8;
+    const size_t rsz = fp64 ? 8 : 4;
+    const int64_t N = ctx->n_steps;
+    int st;
+
+    // V (host or device) -> V^dagger padded, FP64
+    const void *Vd = V;
+    if (!is_device_ptr(V)) {
+        if ((st = ws_reserve(ctx, ctx->gv, (size_t)d * d * esz))) return st;
+        PM_CUDA(cudaMemcpyAsync(ctx->gv.ptr, V, (size_t)d * d * esz, cudaMemcpyHostToDevice, ctx->stream));
+        Vd = ctx->gv.ptr;
+    }
+    if ((st = ws_reserve(ctx, ctx->gvdag, DD * sizeof(double2)))) return st;
+    if (ctx->dtype == PARAMENT_C128)
+        vdag_kernel<double2><<<1, 256, 0, ctx->stream>>>((const double2 *)Vd, d, Dp, (double2 *)ctx->gvdag.ptr);
+    else
+        vdag_kernel<float2><<<1, 256, 0, ctx->stream>>>((const float2 *)Vd, d, Dp, (double2 *)ctx->gvdag.ptr);
+    PM_CUDA(cudaGetLastError());
+
+    // forward pass keeping every leaf and block product
+    const bool host_u = U_out && !is_device_ptr(U_out);
+    if ((st = ws_reserve(ctx, ctx->uout, (size_t)d * d * esz))) return st;
+    void *udst = (U_out && !host_u) ? U_out : ctx->uout.ptr;
+    FusedParams p;
+    int grid = 0, warps = 0, lpb = 0;
+    size_t smem = 0;
+    if ((st = forward_setup(ctx, fp64, udst, p, grid, warps, smem, lpb))) return st;
+    const int64_t L = (int64_t)grid * lpb;
+    if ((st = ws_reserve(ctx, ctx->gleaf, (size_t)L * DD * sizeof(double2)))) return st;
+    if ((st = ws_reserve(ctx, ctx->gblock, (size_t)grid * DD * sizeof(double2)))) return st;
+    if ((st = ws_reserve(ctx, ctx->gbpin, 2 * (size_t)grid * DD * sizeof(double2)))) return st;
+    if ((st = ws_reserve(ctx, ctx->gpin, 2 * (size_t)L * DD * sizeof(double2)))) return st;
+    if ((st = ws_reserve(ctx, ctx->gz, 4 * sizeof(double)))) return st;
+    p.leaf_out = (double2 *)ctx->gleaf.ptr;
+    p.block_out = (double2 *)ctx->gblock.ptr;
+    PM_CUDA(fused_dispatch(Dp, fp64, (int)ctx->integ, p, grid, warps, smem, ctx->stream));
+    record_launch(ctx, ctx->nb_eff, grid, warps, lpb);
+
+    // adjoint launch geometry
+    int aw = 8;
+    while (aw > 1 && adjoint_smem(Dp, fp64, K, aw) > ctx->smem_optin) --aw;
+    const size_t asmem = adjoint_smem(Dp, fp64, K, aw);
+    if (asmem > ctx->smem_optin) return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "adjoint needs %zu B shared memory", asmem);
+    const int abps = adjoint_blocks_per_sm(Dp, fp64, aw, asmem);
+    if (abps <= 0) return set_err(ctx, PARAMENT_ERR_CUDA, "adjoint occupancy query failed");
+    const int agrid = abps * ctx->sm_count;
+    const int64_t TG = (int64_t)agrid * aw * fused_gpw(Dp, fp64);
+    const int64_t maxlen = L > 0 ? (N + L - 1) / L : 0;
+    int64_t c_sub = ctx->opt_grad_subchunk > 0 ? ctx->opt_grad_subchunk : std::max<int64_t>(maxlen, 1);
+    const size_t csz = 2 * rsz;  // complex element
+    const size_t cap = (size_t)ctx->opt_workspace_mb << 20;
+    while (c_sub > 1 && (size_t)TG * c_sub * DD * csz > cap) c_sub = (c_sub + 1) / 2;
+    const int64_t n_ckpt = std::max<int64_t>(1, (maxlen + c_sub - 1) / c_sub);
+    if ((st = ws_reserve(ctx, ctx->gpbuf, (size_t)TG * c_sub * DD * csz))) return st;
+    if ((st = ws_reserve(ctx, ctx->gckpt, (size_t)TG * n_ckpt * DD * csz))) return st;
+
+    void *gdst = grad_out;
+    const bool host_g = !is_device_ptr(grad_out);
+    const size_t gbytes = (size_t)K * N * rsz;
+    if (host_g) {
+        if ((st = ws_reserve(ctx, ctx->ggrad, std::max<size_t>(gbytes, 8)))) return st;
+        gdst = ctx->ggrad.ptr;
+    }
+
+    ScanParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.leafpart = (const double2 *)ctx->gleaf.ptr;
+    sp.blockpart = (const double2 *)ctx->gblock.ptr;
+    sp.n_blocks = grid;
+    sp.leaves_per_block = lpb;
+    sp.bpin = (double2 *)ctx->gbpin.ptr;
+    sp.bsout = sp.bpin + (size_t)grid * DD;
+    sp.pin = (double2 *)ctx->gpin.ptr;
+    sp.sout = sp.pin + (size_t)L * DD;
+    sp.vdag = (const double2 *)ctx->gvdag.ptr;
+    sp.z = (double *)ctx->gz.ptr;
+    sp.U_out = nullptr;
+    sp.d_out = d;
+
+    GradParams gp;
+    std::memset(&gp, 0, sizeof(gp));
+    gp.ctrl = p.ctrl;
+    gp.n_steps = N;
+    gp.K = K;
+    gp.n_basis = ctx->nb_eff;
+    gp.dt = ctx->dt;
+    for (int e = 0; e < kMaxBasis; ++e) gp.slot_of[e] = ctx->slot_of[e];
+    gp.packed = p.packed;
+    gp.bnorm1 = p.bnorm1;
+    gp.hk = (const double2 *)ctx->full.ptr + DD;  // basis entries 1..K are the H_k
+    gp.pin = sp.pin;
+    gp.sout = sp.sout;
+    gp.vdag = sp.vdag;
+    gp.z = sp.z;
+    gp.grad = gdst;
+    gp.pbuf = ctx->gpbuf.ptr;
+    gp.ckpt = ctx->gckpt.ptr;
+    gp.c_sub = (int)c_sub;
+    gp.n_ckpt = (int)n_ckpt;
+    gp.n_leaves = L;
+    gp.d_true = d;
+    gp.status = (unsigned *)ctx->status.ptr;
+    {
+        const double u = fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
+        FusedParams tmp;
+        std::memset(&tmp, 0, sizeof(tmp));
+        build_classes(u, 0, tmp);
+        gp.n_cls = tmp.n_cls;
+        std::memcpy(gp.cls_cap, tmp.cls_cap, sizeof(gp.cls_cap));
+        std::memcpy(gp.cls_code, tmp.cls_code, sizeof(gp.cls_code));
+        std::memcpy(gp.coef_d, tmp.coef_d, sizeof(gp.coef_d));
+        std::memcpy(gp.coef_f, tmp.coef_f, sizeof(gp.coef_f));
+        std::memset(&tmp, 0, sizeof(tmp));
+        build_classes(u, 0, tmp, 1);
+        gp.n_dcls = tmp.n_cls;
+        std::memcpy(gp.dcls_cap, tmp.cls_cap, sizeof(gp.dcls_cap));
+        std::memcpy(gp.dcls_code, tmp.cls_code, sizeof(gp.dcls_code));
+    }
+    PM_CUDA(grad_run(Dp, fp64, sp, gp, agrid, aw, asmem, ctx->stream));
+    ctx->last.grad_subchunk = (int32_t)c_sub;
+
+    if (host_g && gbytes) PM_CUDA(cudaMemcpyAsync(grad_out, gdst, gbytes, cudaMemcpyDeviceToHost, ctx->stream));
+    if (host_u) PM_CUDA(cudaMemcpyAsync(U_out, udst, (size_t)d * d * esz, cudaMemcpyDeviceToHost, ctx->stream));
+    if (loss_out) {
+        double z[4];
+        PM_CUDA(cudaMemcpyAsync(z, ctx->gz.ptr, 3 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        PM_CUDA(cudaStreamSynchronize(ctx->stream));
+        *loss_out = z[2];
+    } else if (host_g || host_u) {
         PM_CUDA(cudaStreamSynchronize(ctx->stream));
     }
     return PARAMENT_OK;
@@ -767,6 +986,14 @@ int parament_set_option(parament_ctx *ctx, int key, int64_t value) {
             if (value < 0) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "tolerance must be >= 0");
             ctx->opt_herm_tol = value;
             return PARAMENT_OK;
+        case PARAMENT_OPT_GRAD_SUBCHUNK:
+            if (value < 0 || value > (1 << 24)) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "sub-chunk in [0, 2^24]");
+            ctx->opt_grad_subchunk = value;
+            return PARAMENT_OK;
+        case PARAMENT_OPT_WORKSPACE_MB:
+            if (value < 1) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "workspace cap must be >= 1 MiB");
+            ctx->opt_workspace_mb = value;
+            return PARAMENT_OK;
     }
     return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown option key %d", key);
 }
@@ -780,6 +1007,8 @@ int parament_get_option(const parament_ctx *ctx, int key, int64_t *value) {
         case PARAMENT_OPT_CHECK_HERMITIAN: *value = ctx->opt_check_herm; return PARAMENT_OK;
         case PARAMENT_OPT_EXTRA_SQUARINGS: *value = ctx->opt_extra_sq; return PARAMENT_OK;
         case PARAMENT_OPT_HERMITIAN_TOL_E12: *value = ctx->opt_herm_tol; return PARAMENT_OK;
+        case PARAMENT_OPT_GRAD_SUBCHUNK: *value = ctx->opt_grad_subchunk; return PARAMENT_OK;
+        case PARAMENT_OPT_WORKSPACE_MB: *value = ctx->opt_workspace_mb; return PARAMENT_OK;
     }
     return PARAMENT_ERR_INVALID_VALUE;
 }

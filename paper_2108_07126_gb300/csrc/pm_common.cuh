@@ -65,6 +65,8 @@ struct FusedParams {
     double2 *partials;         // [gridDim.x][D][D] block partial products (FP64)
     unsigned *tickets;         // >= gridDim.x zero-initialised arrival counters
     void *U_out;               // d_out x d_out
+    double2 *leaf_out;         // optional [n_leaves][D][D]: every leaf product (FP64)
+    double2 *block_out;        // optional [gridDim.x][D][D]: every block product (FP64)
     unsigned long long *counters;
     unsigned *status;
     int extra_squarings;

@@ -125,6 +125,37 @@ __device__ __forceinline__ void mm_tile(const typename Cx<Real>::T *__restrict__
     }
 }
 
+// acc += A * B
+template <typename Real, int D>
+__device__ __forceinline__ void mm_tile_add(const typename Cx<Real>::T *__restrict__ A,
+                                            const typename Cx<Real>::T *__restrict__ B, int rb, int cb,
+                                            typename Cx<Real>::T (&acc)[Geo<Real, D>::TR][Geo<Real, D>::TC]) {
+    using G = Geo<Real, D>;
+    using C = typename G::C;
+    constexpr int TR = G::TR, TC = G::TC, V = G::V, LD = G::LD;
+#pragma unroll
+    for (int k = 0; k < D; k += V) {
+        C a[TR][V], b[V][TC];
+#pragma unroll
+        for (int r = 0; r < TR; ++r) Vec<C, V>::ld(A + (rb + r * G::RBN) * LD + k, a[r]);
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int c = 0; c < TC; c += V) {
+                C t[V];
+                Vec<C, V>::ld(B + (k + v) * LD + G::col(cb, c), t);
+#pragma unroll
+                for (int w = 0; w < V; ++w) b[v][c + w] = t[w];
+            }
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int c = 0; c < TC; ++c) cfma(acc[r][c], a[r][v], b[v][c]);
+    }
+}
+
 template <typename Real, int D>
 __device__ __forceinline__ void st_tile(typename Cx<Real>::T *S, int rb, int cb,
                                         const typename Cx<Real>::T (&t)[Geo<Real, D>::TR][Geo<Real, D>::TC]) {
@@ -446,6 +477,15 @@ __global__ void __launch_bounds__(256, 1) fused_small_kernel(const FusedParams p
         __syncwarp();
     }
 
+    // ---- optional: every leaf product in FP64 (checkpoints of the adjoint pass)
+    if (p.leaf_out) {
+        double2 *dst = p.leaf_out + (size_t)leaf * DD;
+        for (int t = gl; t < DD; t += LANES) {
+            const C v = SR[(t / D) * LD + (t % D)];
+            dst[t] = make_double2((double)v.x, (double)v.y);
+        }
+    }
+
     // ---- statistics and status (before this block's tree arrival)
     if (gl == 0 && n_tree) {
         atomicAdd(&p.counters[0], n_exp);
@@ -476,9 +516,11 @@ __global__ void __launch_bounds__(256, 1) fused_small_kernel(const FusedParams p
     {
         const C *R0 = leaf_R(0);
         double2 *dst = p.partials + (size_t)blockIdx.x * DD;
+        double2 *keep = p.block_out ? p.block_out + (size_t)blockIdx.x * DD : nullptr;
         for (int t = tid; t < DD; t += blockDim.x) {
             const C v = R0[(t / D) * LD + (t % D)];
             dst[t] = make_double2((double)v.x, (double)v.y);
+            if (keep) keep[t] = dst[t];
         }
     }
     __threadfence();
