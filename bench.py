@@ -49,6 +49,7 @@ def parse_args():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--cpu-sample", type=int, default=1 << 16, help="slices in the timed oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
     return ap.parse_args()
 
 
@@ -218,6 +219,49 @@ def time_launches(torch, fn, steps, warmup, flush):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def secondary_workloads(torch, b, wl, dev, flush, steps=10, warmup=3):
+    """Rabi qubit (d = 2, N = 2^14, latency-bound) and the optimal-control gradient (d = 8, N = 65536)."""
+    import numpy as np
+
+    import oracle
+
+    out = {}
+    prop = b.Propagator(dev.index or 0)
+    prob = wl.rabi_qubit()
+    for prec, cdt, rdt in (("fp64", torch.complex128, torch.float64), ("fp32", torch.complex64, torch.float32)):
+        prop.set_hamiltonians(torch.as_tensor(prob.H0).to(cdt), torch.as_tensor(prob.Hk).to(cdt), prob.integrator)
+        prop.set_controls(torch.as_tensor(prob.c).to(rdt).to(dev), prob.dt, prob.n_steps)
+        U = torch.empty(2, 2, dtype=cdt, device=dev)
+        per = time_launches(torch, lambda: prop.propagate(prec, out=U), steps, warmup, flush)
+        ref = oracle.propagate(prob.H0, prob.Hk, prob.c, prob.dt, prob.integrator)
+        err = float(np.max(np.abs(U.cpu().numpy().astype(np.complex128) - ref)))
+        ms = statistics.mean(per)
+        out[f"rabi_qubit_d2_N16384_{prec}"] = {"steps_per_s": prob.n_steps / (ms * 1e-3), "ms_per_step": ms,
+                                                "max_abs_err_vs_oracle": err, "launches_per_step": 1}
+    prob = wl.gradient_qubits()
+    l_ref, g_ref, _ = oracle.loss_and_gradient(prob.H0, prob.Hk, prob.c, prob.dt, prob.V)
+    for prec, cdt, rdt in (("fp64", torch.complex128, torch.float64), ("fp32", torch.complex64, torch.float32)):
+        prop.set_hamiltonians(torch.as_tensor(prob.H0).to(cdt), torch.as_tensor(prob.Hk).to(cdt), "midpoint")
+        prop.set_controls(torch.as_tensor(prob.c).to(rdt).to(dev), prob.dt, prob.n_steps)
+        V = torch.as_tensor(prob.V).to(cdt).to(dev)
+        res = {}
+
+        def step():
+            res["lg"] = prop.propagate_grad(V, prec)
+
+        per = time_launches(torch, step, max(3, steps // 2), 2, flush)
+        loss, grad = res["lg"]
+        g = grad.cpu().numpy().astype(np.float64)
+        ms = statistics.mean(per)
+        out[f"gradient_qubits_d8_N65536_{prec}"] = {
+            "steps_per_s": prob.n_steps / (ms * 1e-3), "ms_per_step": ms,
+            "loss_abs_err_vs_oracle": abs(loss - l_ref),
+            "grad_max_rel_err_vs_oracle": float(np.max(np.abs(g - g_ref)) / np.max(np.abs(g_ref))),
+            "launches_per_step": 5, "timing": "host wall clock incl. the loss read-back"}
+    prop.close()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -284,6 +328,11 @@ def run_ours(args):
     e2e_s = max_over_ranks(statistics.mean(e2e_times), world, dev)
     prop.close()
 
+    # ---- secondary workloads (reported beside the headline, not part of `value`)
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        extra = secondary_workloads(torch, b, wl, dev, flush)
+
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 only
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -323,6 +372,7 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(c_host.numel() * 4),
                 "d2h_bytes_per_step": int(U_host.nbytes)},
+        "secondary": extra,
         "gpu_launches": args.steps,
         "clocks": clk,
         "wall_s_timed": t_wall,

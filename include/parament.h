@@ -160,8 +160,9 @@ int parament_set_stream(parament_ctx *ctx, void *cuda_stream);
  * and choose the integrator (Sec. 6, Parament_setHamiltonian; the Magnus
  * choice makes the library form the commutator basis here, Sec. 4).
  * `dtype` is the storage type of H0/Hk and of every later U_out.  The data are
- * copied; the caller keeps ownership.  d in [1, 16] for this build
- * (PARAMENT_ERR_UNSUPPORTED above), 0 <= K <= 16.  Hk may be NULL when K = 0.
+ * copied; the caller keeps ownership.  1 <= d <= 128 (PARAMENT_ERR_UNSUPPORTED
+ * above; d is padded with zeros to the next power of two, which is exact),
+ * 0 <= K <= 16.  Hk may be NULL when K = 0.
  * Resets any controls set before.  Errors: INVALID_VALUE, NONFINITE,
  * NOT_HERMITIAN (checked on the device; the call waits for the check).
  */
@@ -182,7 +183,10 @@ int parament_set_controls(parament_ctx *ctx, const void *c, parament_real_dtype 
 /*
  * Compute U(T) = U_N ... U_1 into U_out (d x d, the dtype of
  * set_hamiltonians) with arithmetic `prec` (Sec. 2, Eq. slices; Sec. 2.2).
- * One kernel launch: per slice it forms G_j from the control samples, bounds
+ * One kernel launch (d <= 16: groups of lanes of one warp per slice, matrices
+ * in shared memory; d > 16: one thread block per leaf, matrices in an
+ * L2-resident scratch region, products as block-wide tiled GEMMs).  Per
+ * slice it forms G_j from the control samples, bounds
  * ||G_j||_1 in FP64 from the coefficients (Sec. 3.2's triangle-inequality
  * bound, per slice), evaluates a Taylor polynomial of exp(-i G_j / 2^s)
  * (Paterson-Stockmeyer) and squares s times, multiplies consecutive slices in

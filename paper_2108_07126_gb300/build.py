@@ -30,6 +30,9 @@ SOURCES = [
     "pm_grad_d4.cu",
     "pm_grad_d8.cu",
     "pm_grad_d16.cu",
+    "pm_large_d32.cu",
+    "pm_large_d64.cu",
+    "pm_large_d128.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

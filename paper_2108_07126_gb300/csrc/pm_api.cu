@@ -29,13 +29,22 @@ PM_DECL_D(4)
 PM_DECL_D(8)
 PM_DECL_D(16)
 #undef PM_DECL_D
+#define PM_DECL_L(D)                                                                                     \
+    cudaError_t large_dispatch_d##D(int, int, const FusedParams &, void *, int, size_t, cudaStream_t);  \
+    int large_blocks_per_sm_d##D(int, int, size_t);                                                      \
+    size_t large_smem_d##D(int, int);
+PM_DECL_L(32)
+PM_DECL_L(64)
+PM_DECL_L(128)
+#undef PM_DECL_L
 }  // namespace pm
 
 using namespace pm;
 
 namespace {
 
-constexpr int kMaxDim = 16;
+constexpr int kMaxDim = 128;
+constexpr int kMaxSmallDim = 16;  // larger dimensions use one thread block per leaf
 constexpr int kLeafMinSteps = 8;  // fewer blocks for short runs: each leaf gets >= 8 slices
 
 struct Workspace {
@@ -59,7 +68,7 @@ struct parament_ctx {
 
     Workspace hraw, full, packed64, packed32, bnorm, partials, tickets, counters, status, check;
     Workspace ctrl_copy, ctrl_conv, uout, bmax, cpacked64, cpacked32, cbnorm;
-    Workspace gv, gvdag, gleaf, gblock, gbpin, gpin, gz, gpbuf, gckpt, ggrad;
+    Workspace gv, gvdag, gleaf, gblock, gbpin, gpin, gz, gpbuf, gckpt, ggrad, lscratch;
     int nb_eff = 0;
     std::vector<short> slot_of;
 
@@ -146,10 +155,9 @@ bool is_device_ptr(const void *p) {
 }
 
 int pad_dim(int d) {
-    if (d <= 2) return 2;
-    if (d <= 4) return 4;
-    if (d <= 8) return 8;
-    return 16;
+    int D = 2;
+    while (D < d) D *= 2;
+    return D;
 }
 
 int n_basis_for(int K, parament_integrator integ) {
@@ -387,6 +395,31 @@ size_t adjoint_smem(int Dp, int fp64, int K, int warps) {
     }
     return 0;
 }
+cudaError_t large_dispatch(int Dp, int fp64, int integ, const FusedParams &p, void *scratch, int grid, size_t smem,
+                           cudaStream_t st) {
+    switch (Dp) {
+        case 32: return large_dispatch_d32(fp64, integ, p, scratch, grid, smem, st);
+        case 64: return large_dispatch_d64(fp64, integ, p, scratch, grid, smem, st);
+        case 128: return large_dispatch_d128(fp64, integ, p, scratch, grid, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+int large_blocks_per_sm(int Dp, int fp64, int integ, size_t smem) {
+    switch (Dp) {
+        case 32: return large_blocks_per_sm_d32(fp64, integ, smem);
+        case 64: return large_blocks_per_sm_d64(fp64, integ, smem);
+        case 128: return large_blocks_per_sm_d128(fp64, integ, smem);
+    }
+    return 0;
+}
+size_t large_smem(int Dp, int fp64, int nb) {
+    switch (Dp) {
+        case 32: return large_smem_d32(fp64, nb);
+        case 64: return large_smem_d64(fp64, nb);
+        case 128: return large_smem_d128(fp64, nb);
+    }
+    return 0;
+}
 int fused_gpw(int Dp, int fp64) {
     switch (Dp) {
         case 2: return fused_groups_per_warp_d2(fp64);
@@ -504,7 +537,7 @@ int parament_destroy(parament_ctx *ctx) {
                             &ctx->partials, &ctx->tickets, &ctx->counters, &ctx->status, &ctx->check,
                             &ctx->ctrl_copy, &ctx->ctrl_conv, &ctx->uout, &ctx->bmax, &ctx->cpacked64,
                             &ctx->cpacked32, &ctx->cbnorm, &ctx->gv, &ctx->gvdag, &ctx->gleaf, &ctx->gblock,
-                            &ctx->gbpin, &ctx->gpin, &ctx->gz, &ctx->gpbuf, &ctx->gckpt, &ctx->ggrad};
+                            &ctx->gbpin, &ctx->gpin, &ctx->gz, &ctx->gpbuf, &ctx->gckpt, &ctx->ggrad, &ctx->lscratch};
         for (Workspace *w : all) ws_free(*w);
     }
     delete ctx;
@@ -569,7 +602,8 @@ int parament_set_hamiltonians(parament_ctx *ctx, int dim, int n_ctrl, const void
     if ((st = ws_reserve(ctx, ctx->packed64, nb * DD * sizeof(double)))) return st;
     if ((st = ws_reserve(ctx, ctx->packed32, nb * DD * sizeof(float)))) return st;
     if ((st = ws_reserve(ctx, ctx->bnorm, nb * sizeof(double)))) return st;
-    if ((st = ws_reserve(ctx, ctx->partials, (size_t)ctx->max_grid * DD * sizeof(double2)))) return st;
+    const int grid_cap = Dp <= kMaxSmallDim ? ctx->max_grid : 2 * ctx->sm_count;
+    if ((st = ws_reserve(ctx, ctx->partials, (size_t)grid_cap * DD * sizeof(double2)))) return st;
     const int magnus = integrator != PARAMENT_MIDPOINT;
     if (dtype == PARAMENT_C128)
         build_basis_kernel<double2><<<nb, 256, 0, ctx->stream>>>((const double2 *)ctx->hraw.ptr, dim, Dp, n_ctrl,
@@ -683,6 +717,21 @@ int forward_setup(parament_ctx *ctx, int fp64, void *U_dst, FusedParams &p, int 
         return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "Taylor degree %lld is not one of 1, 2, 4, 6, 9, 12",
                        (long long)ctx->opt_degree);
 
+    if (Dp > kMaxSmallDim) {
+        // one thread block (256 threads) per leaf; working matrices in a per-block scratch region
+        warps = 8;
+        smem = large_smem(Dp, fp64, nb);
+        if (smem > ctx->smem_optin) return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "large-d shared memory %zu B", smem);
+        const int bps = large_blocks_per_sm(Dp, fp64, (int)ctx->integ, smem);
+        if (bps <= 0) return set_err(ctx, PARAMENT_ERR_CUDA, "occupancy query failed (large d)");
+        leaves_per_block = 1;
+        grid = (int)ctx->opt_grid;
+        if (grid <= 0) grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_steps, (int64_t)bps * ctx->sm_count));
+        grid = std::min(grid, 2 * ctx->sm_count);
+        const size_t csz = fp64 ? sizeof(double2) : sizeof(float2);
+        int st = ws_reserve(ctx, ctx->lscratch, (size_t)grid * 6 * Dp * Dp * csz);
+        if (st) return st;
+    } else {
     warps = (int)ctx->opt_warps;
     if (warps <= 0) {
         warps = 8;
@@ -703,6 +752,7 @@ int forward_setup(parament_ctx *ctx, int fp64, void *U_dst, FusedParams &p, int 
         grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)bps * ctx->sm_count));
     }
     grid = std::min(grid, ctx->max_grid);
+    }
 
     p.ctrl = ctrl;
     p.S = ctx->S;
@@ -723,6 +773,12 @@ int forward_setup(parament_ctx *ctx, int fp64, void *U_dst, FusedParams &p, int 
     p.status = (unsigned *)ctx->status.ptr;
     p.extra_squarings = (int)ctx->opt_extra_sq;
     return PARAMENT_OK;
+}
+
+cudaError_t forward_launch(parament_ctx *ctx, int fp64, const FusedParams &p, int grid, int warps, size_t smem) {
+    if (ctx->dpad > kMaxSmallDim)
+        return large_dispatch(ctx->dpad, fp64, (int)ctx->integ, p, ctx->lscratch.ptr, grid, smem, ctx->stream);
+    return fused_dispatch(ctx->dpad, fp64, (int)ctx->integ, p, grid, warps, smem, ctx->stream);
 }
 
 void record_launch(parament_ctx *ctx, int nb, int grid, int warps, int leaves_per_block) {
@@ -782,7 +838,7 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) 
     size_t smem = 0;
     int st = forward_setup(ctx, fp64, dst, p, grid, warps, smem, lpb);
     if (st) return st;
-    PM_CUDA(fused_dispatch(ctx->dpad, fp64, (int)ctx->integ, p, grid, warps, smem, ctx->stream));
+    PM_CUDA(forward_launch(ctx, fp64, p, grid, warps, smem));
     record_launch(ctx, ctx->nb_eff, grid, warps, lpb);
 
     if (host_out) {
@@ -802,6 +858,8 @@ int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, 
         return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "the adjoint gradient covers the midpoint rule");
     if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32)
         return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "gradient precision must be FP64 or FP32");
+    if (ctx->dpad > kMaxSmallDim)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "the adjoint gradient covers d <= %d", kMaxSmallDim);
     DeviceGuard guard(ctx->device);
     const int fp64 = prec == PARAMENT_PREC_FP64;
     const int Dp = ctx->dpad, d = ctx->dim, K = ctx->K;

@@ -185,20 +185,19 @@ template <> __device__ __forceinline__ double pow2neg<double>(int s) {
 
 // Effective coefficients gamma_e of one slice (Sec. 4, Eq. magnus_coeffs with the
 // commutator sign of Omega_2): basis order H0, H_k, i[H0,H_k], i[H_k,H_k'] (k < k').
-template <typename Real, int INTEG>
-__device__ __forceinline__ void slice_coefficients(const FusedParams &p, int64_t j, bool active,
-                                                   Real *gam /* stride 32 */) {
+template <typename Real, int INTEG, int STRIDE = 32>
+__device__ __forceinline__ void slice_coefficients(const FusedParams &p, int64_t j, bool active, Real *gam) {
     const Real *c = (const Real *)p.ctrl;
     const int K = p.K;
     const Real h = (Real)p.dt;
     if (!active) {
-        for (int e = 0; e < p.n_basis; ++e) gam[e * 32] = Real(0);
+        for (int e = 0; e < p.n_basis; ++e) gam[e * STRIDE] = Real(0);
         return;
     }
     // coefficients of identically zero basis matrices are dropped
     auto put = [&](int e, Real v) {
         const int sl = p.slot_of[e];
-        if (sl >= 0) gam[sl * 32] = v;
+        if (sl >= 0) gam[sl * STRIDE] = v;
     };
     put(0, h);
     if (INTEG == kMidpoint) {

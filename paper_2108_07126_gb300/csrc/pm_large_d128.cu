@@ -1,0 +1,41 @@
+// Instantiations of the large-dimension propagation kernel for padded dimension 128.
+#include "pm_large.cuh"
+
+namespace pm {
+
+cudaError_t large_dispatch_d128(int fp64, int integ, const FusedParams &p, void *scratch, int grid, size_t smem,
+                               cudaStream_t st) {
+    switch (integ * 2 + (fp64 ? 1 : 0)) {
+        case 0: return launch_large<float, 128, kMidpoint>(p, scratch, grid, smem, st);
+        case 1: return launch_large<double, 128, kMidpoint>(p, scratch, grid, smem, st);
+        case 2: return launch_large<float, 128, kGL2>(p, scratch, grid, smem, st);
+        case 3: return launch_large<double, 128, kGL2>(p, scratch, grid, smem, st);
+        case 4: return launch_large<float, 128, kSimpson>(p, scratch, grid, smem, st);
+        case 5: return launch_large<double, 128, kSimpson>(p, scratch, grid, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int large_blocks_per_sm_d128(int fp64, int integ, size_t smem) {
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    auto q = [&](auto k) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kLargeThreads, smem);
+    };
+    switch (integ * 2 + (fp64 ? 1 : 0)) {
+        case 0: q(large_kernel<float, 128, kMidpoint>); break;
+        case 1: q(large_kernel<double, 128, kMidpoint>); break;
+        case 2: q(large_kernel<float, 128, kGL2>); break;
+        case 3: q(large_kernel<double, 128, kGL2>); break;
+        case 4: q(large_kernel<float, 128, kSimpson>); break;
+        case 5: q(large_kernel<double, 128, kSimpson>); break;
+    }
+    return e == cudaSuccess ? nb : 0;
+}
+
+size_t large_smem_d128(int fp64, int n_basis) {
+    return fp64 ? large_smem_bytes<double, 128>(n_basis) : large_smem_bytes<float, 128>(n_basis);
+}
+
+}  // namespace pm

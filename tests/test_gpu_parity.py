@@ -210,7 +210,7 @@ def test_state_machine_and_errors(prop, torch):
         Hok = torch.eye(2, dtype=torch.complex128, device="cuda")
         assert b.raw_call("parament_set_hamiltonians", ctx, 0, 0, Hok.data_ptr(), None, 1, 0) == \
             b.PARAMENT_ERR_INVALID_VALUE
-        assert b.raw_call("parament_set_hamiltonians", ctx, 64, 0, Hok.data_ptr(), None, 1, 0) == \
+        assert b.raw_call("parament_set_hamiltonians", ctx, 256, 0, Hok.data_ptr(), None, 1, 0) == \
             b.PARAMENT_ERR_UNSUPPORTED
         assert b.raw_call("parament_set_controls", ctx, None, 1, 4, 0.1) == b.PARAMENT_ERR_STATE
         assert b.raw_call("parament_set_hamiltonians", ctx, 2, 0, Hok.data_ptr(), None, 1, 0) == b.PARAMENT_OK
@@ -242,6 +242,45 @@ def test_mixed_control_dtypes(prop, torch):
     assert np.max(np.abs(U - r)) <= TOL64
     U = run(prop, prob, "fp32", c_dtype=torch.float64, h_dtype=torch.complex128)
     assert np.max(np.abs(U - ref(prob))) <= tol32(4, 200)
+
+
+# --- dimensions above 16: one thread block per leaf ------------------------------------------------
+
+
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+@pytest.mark.parametrize("d", [17, 32, 40, 64, 100, 128])
+def test_large_d_fp64_matches_oracle(prop, integrator, d):
+    n = 37 if d <= 64 else 9
+    prob = wl.random_problem(d, 2, n, integrator, seed=600 + d, g_norm=0.6)
+    U = run(prop, prob, "fp64")
+    assert np.max(np.abs(U - ref(prob))) <= TOL64
+
+
+@pytest.mark.parametrize("d", [32, 64, 128])
+def test_large_d_fp32_matches_oracle(prop, d):
+    n = 301 if d <= 64 else 41
+    prob = wl.random_problem(d, 3, n, "magnus4_gl2", seed=700 + d, g_norm=0.5)
+    U = run(prop, prob, "fp32")
+    assert np.max(np.abs(U - ref32(prob))) <= tol32(d, n)
+
+
+@pytest.mark.parametrize("grid", [1, 2, 3, 7, 152])
+def test_large_d_tree_shapes(prop, grid):
+    from paper_2108_07126_gb300 import binding as b
+
+    prob = wl.random_problem(48, 2, 200, "midpoint", seed=800, g_norm=0.3)
+    prop.set_option(b.PARAMENT_OPT_GRID_BLOCKS, grid)
+    U = run(prop, prob, "fp64")
+    assert np.max(np.abs(U - ref(prob))) <= TOL64
+    st = prop.stats()
+    assert st["grid_blocks"] == min(grid, 200) and st["tree_products"] == 200
+
+
+def test_large_d_big_norm_squarings(prop):
+    prob = wl.random_problem(64, 1, 5, "midpoint", seed=801, g_norm=20.0)
+    U = run(prop, prob, "fp64")
+    assert np.max(np.abs(U - ref(prob))) <= 20 * TOL64
+    assert prop.stats()["max_squarings"] >= 4
 
 
 # --- the benchmark workloads -------------------------------------------------------------------
