@@ -83,9 +83,11 @@ typedef enum {
  *  FP32: exponent assembly, exponential and the in-block tree in float; the
  *        norm bound that picks the Taylor degree and the number of squarings,
  *        and the product tree above the thread-block level, in double.
- *  FP32_TC_*: FP32 with the complex products of d >= 32 on tensor cores
- *        (split operands, FP32 accumulation).  Not implemented in this build:
- *        PARAMENT_ERR_UNSUPPORTED.
+ *  FP32_TC_TF32X3: FP32 with the complex products of d >= 32 on the tensor
+ *        cores: every FP32 operand split into two TF32 terms, three MMAs per
+ *        real product (hi*hi + hi*lo + lo*hi), FP32 accumulation; FP64 norm
+ *        bound and FP64 top tree as in FP32.  d < 32: PARAMENT_ERR_UNSUPPORTED.
+ *  FP32_TC_BF16X3: not implemented in this build (PARAMENT_ERR_UNSUPPORTED).
  */
 typedef enum {
     PARAMENT_PREC_FP64 = 0,

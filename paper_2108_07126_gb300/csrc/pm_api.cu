@@ -30,8 +30,8 @@ PM_DECL_D(8)
 PM_DECL_D(16)
 #undef PM_DECL_D
 #define PM_DECL_L(D)                                                                                     \
-    cudaError_t large_dispatch_d##D(int, int, const FusedParams &, void *, int, size_t, cudaStream_t);  \
-    int large_blocks_per_sm_d##D(int, int, size_t);                                                      \
+    cudaError_t large_dispatch_d##D(int, int, const FusedParams &, void *, int, size_t, cudaStream_t, int); \
+    int large_blocks_per_sm_d##D(int, int, size_t, int);                                                 \
     size_t large_smem_d##D(int, int);
 PM_DECL_L(32)
 PM_DECL_L(64)
@@ -396,19 +396,19 @@ size_t adjoint_smem(int Dp, int fp64, int K, int warps) {
     return 0;
 }
 cudaError_t large_dispatch(int Dp, int fp64, int integ, const FusedParams &p, void *scratch, int grid, size_t smem,
-                           cudaStream_t st) {
+                           cudaStream_t st, int tc) {
     switch (Dp) {
-        case 32: return large_dispatch_d32(fp64, integ, p, scratch, grid, smem, st);
-        case 64: return large_dispatch_d64(fp64, integ, p, scratch, grid, smem, st);
-        case 128: return large_dispatch_d128(fp64, integ, p, scratch, grid, smem, st);
+        case 32: return large_dispatch_d32(fp64, integ, p, scratch, grid, smem, st, tc);
+        case 64: return large_dispatch_d64(fp64, integ, p, scratch, grid, smem, st, tc);
+        case 128: return large_dispatch_d128(fp64, integ, p, scratch, grid, smem, st, tc);
     }
     return cudaErrorInvalidValue;
 }
-int large_blocks_per_sm(int Dp, int fp64, int integ, size_t smem) {
+int large_blocks_per_sm(int Dp, int fp64, int integ, size_t smem, int tc) {
     switch (Dp) {
-        case 32: return large_blocks_per_sm_d32(fp64, integ, smem);
-        case 64: return large_blocks_per_sm_d64(fp64, integ, smem);
-        case 128: return large_blocks_per_sm_d128(fp64, integ, smem);
+        case 32: return large_blocks_per_sm_d32(fp64, integ, smem, tc);
+        case 64: return large_blocks_per_sm_d64(fp64, integ, smem, tc);
+        case 128: return large_blocks_per_sm_d128(fp64, integ, smem, tc);
     }
     return 0;
 }
@@ -692,7 +692,7 @@ namespace {
 // Controls in the compute type, Taylor table and launch geometry of the fused
 // forward kernel (shared by propagate and propagate_grad).
 int forward_setup(parament_ctx *ctx, int fp64, void *U_dst, FusedParams &p, int &grid, int &warps, size_t &smem,
-                  int &leaves_per_block) {
+                  int &leaves_per_block, int tc = 0) {
     const int Dp = ctx->dpad, nb = ctx->nb_eff;
     const void *ctrl = ctx->ctrl;
     const int64_t count = (int64_t)ctx->K * ctx->S;
@@ -722,7 +722,7 @@ int forward_setup(parament_ctx *ctx, int fp64, void *U_dst, FusedParams &p, int 
         warps = 8;
         smem = large_smem(Dp, fp64, nb);
         if (smem > ctx->smem_optin) return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "large-d shared memory %zu B", smem);
-        const int bps = large_blocks_per_sm(Dp, fp64, (int)ctx->integ, smem);
+        const int bps = large_blocks_per_sm(Dp, fp64, (int)ctx->integ, smem, tc);
         if (bps <= 0) return set_err(ctx, PARAMENT_ERR_CUDA, "occupancy query failed (large d)");
         leaves_per_block = 1;
         grid = (int)ctx->opt_grid;
@@ -775,9 +775,10 @@ int forward_setup(parament_ctx *ctx, int fp64, void *U_dst, FusedParams &p, int 
     return PARAMENT_OK;
 }
 
-cudaError_t forward_launch(parament_ctx *ctx, int fp64, const FusedParams &p, int grid, int warps, size_t smem) {
+cudaError_t forward_launch(parament_ctx *ctx, int fp64, const FusedParams &p, int grid, int warps, size_t smem,
+                           int tc = 0) {
     if (ctx->dpad > kMaxSmallDim)
-        return large_dispatch(ctx->dpad, fp64, (int)ctx->integ, p, ctx->lscratch.ptr, grid, smem, ctx->stream);
+        return large_dispatch(ctx->dpad, fp64, (int)ctx->integ, p, ctx->lscratch.ptr, grid, smem, ctx->stream, tc);
     return fused_dispatch(ctx->dpad, fp64, (int)ctx->integ, p, grid, warps, smem, ctx->stream);
 }
 
@@ -815,12 +816,15 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) 
     ctx->err.clear();
     if (ctx->state < 2) return set_err(ctx, PARAMENT_ERR_STATE, "set_hamiltonians and set_controls must come first");
     if (!U_out) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "null U_out");
-    if (prec == PARAMENT_PREC_FP32_TC_BF16X3 || prec == PARAMENT_PREC_FP32_TC_TF32X3)
-        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "tensor-core precision modes need d >= 32; not in this build");
-    if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32)
+    if (prec == PARAMENT_PREC_FP32_TC_BF16X3)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "split-BF16 tensor-core products are not in this build");
+    if (prec == PARAMENT_PREC_FP32_TC_TF32X3 && ctx->dpad <= kMaxSmallDim)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "tensor-core products are used for d >= 32 only");
+    if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32 && prec != PARAMENT_PREC_FP32_TC_TF32X3)
         return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown precision %d", (int)prec);
     DeviceGuard guard(ctx->device);
     const int fp64 = prec == PARAMENT_PREC_FP64;
+    const int tc = prec == PARAMENT_PREC_FP32_TC_TF32X3;
 
     const size_t esz = ctx->dtype == PARAMENT_C128 ? 16 : 8;
     const bool host_out = !is_device_ptr(U_out);
@@ -836,9 +840,9 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) 
     FusedParams p;
     int grid = 0, warps = 0, lpb = 0;
     size_t smem = 0;
-    int st = forward_setup(ctx, fp64, dst, p, grid, warps, smem, lpb);
+    int st = forward_setup(ctx, fp64, dst, p, grid, warps, smem, lpb, tc);
     if (st) return st;
-    PM_CUDA(forward_launch(ctx, fp64, p, grid, warps, smem));
+    PM_CUDA(forward_launch(ctx, fp64, p, grid, warps, smem, tc));
     record_launch(ctx, ctx->nb_eff, grid, warps, lpb);
 
     if (host_out) {

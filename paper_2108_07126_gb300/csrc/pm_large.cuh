@@ -11,6 +11,8 @@
 // memory (cp.async, double-buffered) and accumulates register tiles.
 #pragma once
 
+#include <type_traits>
+
 #include "pm_fused.cuh"
 
 namespace pm {
@@ -42,11 +44,15 @@ template <typename Real, int D> struct LGeo {
     static constexpr size_t PANEL_BYTES = (size_t)2 * (AS + BS) * sizeof(C);  // double-buffered
 };
 
+template <int D> struct TcGeo;
+
 template <typename Real, int D>
 __host__ __device__ inline size_t large_panel_bytes() {
-    // the FP64 top tree runs its products through the same panels
-    return LGeo<Real, D>::PANEL_BYTES > LGeo<double, D>::PANEL_BYTES ? LGeo<Real, D>::PANEL_BYTES
-                                                                      : LGeo<double, D>::PANEL_BYTES;
+    // the FP64 top tree and the tensor-core products run through the same panels
+    size_t b = LGeo<Real, D>::PANEL_BYTES;
+    if (LGeo<double, D>::PANEL_BYTES > b) b = LGeo<double, D>::PANEL_BYTES;
+    if (TcGeo<D>::PANEL_BYTES > b) b = TcGeo<D>::PANEL_BYTES;
+    return b;
 }
 
 template <typename Real, int D>
@@ -130,7 +136,158 @@ __device__ void cta_mm(const typename Cx<Real>::T *__restrict__ A, const typenam
     __syncthreads();
 }
 
-template <typename Real, int D, int INTEG>
+// ---------------------------------------------------------------- tensor-core product (3xTF32)
+//
+// FP32 complex product on the tensor cores with FP32 accuracy: every operand
+// x = hi + lo with hi = tf32(x), lo = tf32(x - hi) (Ootomo & Yokota's split),
+// x*y ~ hi_x hi_y + hi_x lo_y + lo_x hi_y, accumulated in FP32.  The complex
+// product takes four real products (Re = Re Re - Im Im, Im = Re Im + Im Re),
+// so 12 m16n8k8 TF32 MMAs per 16x8x8 complex tile step.
+template <int D> struct TcTile;
+template <> struct TcTile<32> { static constexpr int PASS = 1, WM = 2, WN = 4; };
+template <> struct TcTile<64> { static constexpr int PASS = 1, WM = 2, WN = 4; };
+template <> struct TcTile<128> { static constexpr int PASS = 2, WM = 2, WN = 4; };
+
+template <int D> struct TcGeo {
+    static constexpr int PASS = TcTile<D>::PASS, WM = TcTile<D>::WM, WN = TcTile<D>::WN;
+    static constexpr int RBAND = D / PASS, WTM = RBAND / WM, WTN = D / WN;
+    static constexpr int MT = WTM / 16, NT = WTN / 8;
+    static constexpr int KP = 16, ALD = KP + 4, BLD = D + 4;
+    static constexpr int AS = RBAND * ALD, BS = KP * BLD;
+    static constexpr size_t PANEL_BYTES = (size_t)2 * (AS + BS) * sizeof(float2);
+    static_assert(WM * WN * 32 == kLargeThreads && MT >= 1 && NT >= 1, "warp tiling");
+};
+
+__device__ __forceinline__ unsigned tf32_rna(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
+    hi = tf32_rna(x);
+    lo = tf32_rna(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// d += hi_a hi_b + hi_a lo_b + lo_a hi_b
+__device__ __forceinline__ void mma3(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4],
+                                     const unsigned (&bh)[2], const unsigned (&bl)[2]) {
+    mma_tf32(d, al, bh);
+    mma_tf32(d, ah, bl);
+    mma_tf32(d, ah, bh);
+}
+
+template <int D>
+__device__ void cta_mm_tc(const float2 *__restrict__ A, const float2 *__restrict__ B, float2 *__restrict__ Cout,
+                          unsigned char *panels) {
+    using G = TcGeo<D>;
+    constexpr int KP = G::KP, ALD = G::ALD, BLD = G::BLD, RBAND = G::RBAND, MT = G::MT, NT = G::NT;
+    float2 *As[2] = {(float2 *)panels, (float2 *)panels + G::AS};
+    float2 *Bs[2] = {(float2 *)panels + 2 * G::AS, (float2 *)panels + 2 * G::AS + G::BS};
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp / G::WN, wn = warp % G::WN;
+    const int gq = lane >> 2, tq = lane & 3;  // group id, thread in group (fragment layout)
+
+    for (int pass = 0; pass < G::PASS; ++pass) {
+        const int row0 = pass * RBAND;
+        auto load = [&](int buf, int k0) {
+            for (int e = tid; e < RBAND * KP / 2; e += kLargeThreads) {
+                const int r = e / (KP / 2), c = (e % (KP / 2)) * 2;
+                cp_async16(As[buf] + r * ALD + c, A + (size_t)(row0 + r) * D + k0 + c);
+            }
+            for (int e = tid; e < KP * D / 2; e += kLargeThreads) {
+                const int r = e / (D / 2), c = (e % (D / 2)) * 2;
+                cp_async16(Bs[buf] + r * BLD + c, B + (size_t)(k0 + r) * D + c);
+            }
+            cp_async_commit();
+        };
+        float accr[MT][NT][4], acci[MT][NT][4];
+#pragma unroll
+        for (int i = 0; i < MT; ++i)
+#pragma unroll
+            for (int j = 0; j < NT; ++j)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) accr[i][j][v] = acci[i][j][v] = 0.f;
+        load(0, 0);
+        for (int kp = 0; kp < D / KP; ++kp) {
+            const int buf = kp & 1;
+            if (kp + 1 < D / KP) {
+                load(buf ^ 1, (kp + 1) * KP);
+                cp_async_wait_one();
+            } else {
+                cp_async_wait_all();
+            }
+            __syncthreads();
+            const float2 *a_s = As[buf], *b_s = Bs[buf];
+#pragma unroll
+            for (int kk = 0; kk < KP; kk += 8) {
+                unsigned arh[MT][4], arl[MT][4], aih[MT][4], ail[MT][4], nih[MT][4], nil[MT][4];
+#pragma unroll
+                for (int i = 0; i < MT; ++i) {
+                    const int r0 = wm * G::WTM + i * 16 + gq;
+                    const float2 v0 = a_s[r0 * ALD + kk + tq], v1 = a_s[(r0 + 8) * ALD + kk + tq];
+                    const float2 v2 = a_s[r0 * ALD + kk + tq + 4], v3 = a_s[(r0 + 8) * ALD + kk + tq + 4];
+                    const float re[4] = {v0.x, v1.x, v2.x, v3.x}, im[4] = {v0.y, v1.y, v2.y, v3.y};
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        split_tf32(re[v], arh[i][v], arl[i][v]);
+                        split_tf32(im[v], aih[i][v], ail[i][v]);
+                        nih[i][v] = aih[i][v] ^ 0x80000000u;  // -Im A, exact
+                        nil[i][v] = ail[i][v] ^ 0x80000000u;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < NT; ++j) {
+                    const int n = wn * G::WTN + j * 8 + gq;
+                    const float2 w0 = b_s[(kk + tq) * BLD + n], w1 = b_s[(kk + tq + 4) * BLD + n];
+                    unsigned brh[2], brl[2], bih[2], bil[2];
+                    split_tf32(w0.x, brh[0], brl[0]);
+                    split_tf32(w1.x, brh[1], brl[1]);
+                    split_tf32(w0.y, bih[0], bil[0]);
+                    split_tf32(w1.y, bih[1], bil[1]);
+#pragma unroll
+                    for (int i = 0; i < MT; ++i) {
+                        mma3(accr[i][j], arh[i], arl[i], brh, brl);  // + Re A Re B
+                        mma3(accr[i][j], nih[i], nil[i], bih, bil);  // - Im A Im B
+                        mma3(acci[i][j], arh[i], arl[i], bih, bil);  // + Re A Im B
+                        mma3(acci[i][j], aih[i], ail[i], brh, brl);  // + Im A Re B
+                    }
+                }
+            }
+            __syncthreads();
+        }
+#pragma unroll
+        for (int i = 0; i < MT; ++i)
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const int r = row0 + wm * G::WTM + i * 16 + gq;
+                const int c = wn * G::WTN + j * 8 + 2 * tq;
+                Cout[(size_t)r * D + c] = make_float2(accr[i][j][0], acci[i][j][0]);
+                Cout[(size_t)r * D + c + 1] = make_float2(accr[i][j][1], acci[i][j][1]);
+                Cout[(size_t)(r + 8) * D + c] = make_float2(accr[i][j][2], acci[i][j][2]);
+                Cout[(size_t)(r + 8) * D + c + 1] = make_float2(accr[i][j][3], acci[i][j][3]);
+            }
+    }
+    __syncthreads();
+}
+
+// the complex product used by the large kernel: CUDA cores, or 3xTF32 tensor cores (FP32 only)
+template <typename Real, int D, bool TC>
+__device__ __forceinline__ void large_mm(const typename Cx<Real>::T *A, const typename Cx<Real>::T *B,
+                                         typename Cx<Real>::T *Cout, unsigned char *panels) {
+    if constexpr (TC && std::is_same<Real, float>::value) cta_mm_tc<D>(A, B, Cout, panels);
+    else cta_mm<Real, D>(A, B, Cout, panels);
+}
+
+template <typename Real, int D, int INTEG, bool TC = false>
 __global__ void __launch_bounds__(kLargeThreads, 1) large_kernel(const FusedParams p, void *scratch) {
     using G = LGeo<Real, D>;
     using C = typename G::C;
@@ -183,8 +340,8 @@ __global__ void __launch_bounds__(kLargeThreads, 1) large_kernel(const FusedPara
             SX[e] = Cx<Real>::make(im * sc, -re * sc);
         }
         __syncthreads();
-        if (q >= 2) cta_mm<Real, D>(SX, SX, SX2, panels);
-        if (q >= 3) cta_mm<Real, D>(SX2, SX, SX3, panels);
+        if (q >= 2) large_mm<Real, D, TC>(SX, SX, SX2, panels);
+        if (q >= 3) large_mm<Real, D, TC>(SX2, SX, SX3, panels);
         const C *Xq = (q == 1) ? SX : ((q == 2) ? SX2 : SX3);
         // Horner over blocks with two ping-pong buffers P0 / P1:
         //   T = a_{q r} X^q + B_{r-1};  T <- X^q T + B_b;  B_b = sum_{l<q} a_{q b + l} X^l
@@ -214,16 +371,16 @@ __global__ void __launch_bounds__(kLargeThreads, 1) large_kernel(const FusedPara
         C *cur = P0, *nxt = P1;
         add_block(cur, Xq, coef<Real>(p, q * rh), rh - 1);
         for (int b = rh - 2; b >= 0; --b) {
-            cta_mm<Real, D>(Xq, cur, nxt, panels);
+            large_mm<Real, D, TC>(Xq, cur, nxt, panels);
             add_block(nxt, nxt, Real(1), b);
             C *t2 = cur; cur = nxt; nxt = t2;
         }
         for (int i = 0; i < s; ++i) {
-            cta_mm<Real, D>(cur, cur, nxt, panels);
+            large_mm<Real, D, TC>(cur, cur, nxt, panels);
             C *t2 = cur; cur = nxt; nxt = t2;
         }
         // leaf product R <- U_j R
-        cta_mm<Real, D>(cur, SR, nxt, panels);
+        large_mm<Real, D, TC>(cur, SR, nxt, panels);
         for (int e = tid; e < DD; e += kLargeThreads) SR[e] = nxt[e];
         __syncthreads();
         if (tid == 0) {
@@ -297,9 +454,9 @@ __global__ void __launch_bounds__(kLargeThreads, 1) large_kernel(const FusedPara
     }
 }
 
-template <typename Real, int D, int INTEG>
+template <typename Real, int D, int INTEG, bool TC = false>
 cudaError_t launch_large(const FusedParams &p, void *scratch, int grid, size_t smem, cudaStream_t st) {
-    auto k = large_kernel<Real, D, INTEG>;
+    auto k = large_kernel<Real, D, INTEG, TC>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, kLargeThreads, smem, st>>>(p, scratch);

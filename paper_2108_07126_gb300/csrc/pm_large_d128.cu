@@ -4,7 +4,15 @@
 namespace pm {
 
 cudaError_t large_dispatch_d128(int fp64, int integ, const FusedParams &p, void *scratch, int grid, size_t smem,
-                               cudaStream_t st) {
+                               cudaStream_t st, int tc) {
+    if (tc && !fp64) {
+        switch (integ) {
+            case kMidpoint: return launch_large<float, 128, kMidpoint, true>(p, scratch, grid, smem, st);
+            case kGL2: return launch_large<float, 128, kGL2, true>(p, scratch, grid, smem, st);
+            case kSimpson: return launch_large<float, 128, kSimpson, true>(p, scratch, grid, smem, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (integ * 2 + (fp64 ? 1 : 0)) {
         case 0: return launch_large<float, 128, kMidpoint>(p, scratch, grid, smem, st);
         case 1: return launch_large<double, 128, kMidpoint>(p, scratch, grid, smem, st);
@@ -16,13 +24,21 @@ cudaError_t large_dispatch_d128(int fp64, int integ, const FusedParams &p, void 
     return cudaErrorInvalidValue;
 }
 
-int large_blocks_per_sm_d128(int fp64, int integ, size_t smem) {
+int large_blocks_per_sm_d128(int fp64, int integ, size_t smem, int tc) {
     int nb = 0;
     cudaError_t e = cudaErrorInvalidValue;
     auto q = [&](auto k) {
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kLargeThreads, smem);
     };
+    if (tc && !fp64) {
+        switch (integ) {
+            case kMidpoint: q(large_kernel<float, 128, kMidpoint, true>); break;
+            case kGL2: q(large_kernel<float, 128, kGL2, true>); break;
+            case kSimpson: q(large_kernel<float, 128, kSimpson, true>); break;
+        }
+        return e == cudaSuccess ? nb : 0;
+    }
     switch (integ * 2 + (fp64 ? 1 : 0)) {
         case 0: q(large_kernel<float, 128, kMidpoint>); break;
         case 1: q(large_kernel<double, 128, kMidpoint>); break;

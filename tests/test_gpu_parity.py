@@ -264,6 +264,29 @@ def test_large_d_fp32_matches_oracle(prop, d):
     assert np.max(np.abs(U - ref32(prob))) <= tol32(d, n)
 
 
+@pytest.mark.parametrize("d", [32, 64, 128])
+def test_tensor_core_tf32x3_matches_oracle(prop, d):
+    """3xTF32 tensor-core products keep FP32 accuracy."""
+    n = 301 if d <= 64 else 41
+    prob = wl.random_problem(d, 3, n, "magnus4_gl2", seed=900 + d, g_norm=0.5)
+    U = run(prop, prob, "fp32_tc_tf32x3", c_dtype=__import__("torch").float32,
+            h_dtype=__import__("torch").complex64)
+    assert np.max(np.abs(U - ref32(prob))) <= 2 * tol32(d, n)
+
+
+def test_tensor_core_modes_rejected_where_not_built(prop, torch):
+    from paper_2108_07126_gb300 import binding as b
+
+    prob = wl.random_problem(16, 1, 10, "midpoint", seed=1)
+    with pytest.raises(b.ParamentError) as e:
+        run(prop, prob, "fp32_tc_tf32x3", c_dtype=torch.float32, h_dtype=torch.complex64)
+    assert e.value.status == b.PARAMENT_ERR_UNSUPPORTED
+    prob = wl.random_problem(32, 1, 10, "midpoint", seed=1)
+    with pytest.raises(b.ParamentError) as e:
+        run(prop, prob, "fp32_tc_bf16x3", c_dtype=torch.float32, h_dtype=torch.complex64)
+    assert e.value.status == b.PARAMENT_ERR_UNSUPPORTED
+
+
 @pytest.mark.parametrize("grid", [1, 2, 3, 7, 152])
 def test_large_d_tree_shapes(prop, grid):
     from paper_2108_07126_gb300 import binding as b
