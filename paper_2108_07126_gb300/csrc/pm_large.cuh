@@ -120,7 +120,7 @@ __device__ void cta_mm(const typename Cx<Real>::T *__restrict__ A, const typenam
 #pragma unroll
                 for (int r = 0; r < TR; ++r) a[r] = a_s[(ty + r * TY) * ALD + k];
 #pragma unroll
-                for (int c = 0; c < TC; ++c) b[c] = b_s[k * BLD + tx * TC + c];
+                for (int c = 0; c < TC; ++c) b[c] = b_s[k * BLD + tx + c * G::TX];
 #pragma unroll
                 for (int r = 0; r < TR; ++r)
 #pragma unroll
@@ -131,7 +131,7 @@ __device__ void cta_mm(const typename Cx<Real>::T *__restrict__ A, const typenam
 #pragma unroll
         for (int r = 0; r < TR; ++r)
 #pragma unroll
-            for (int c = 0; c < TC; ++c) Cout[(size_t)(row0 + ty + r * TY) * D + tx * TC + c] = acc[r][c];
+            for (int c = 0; c < TC; ++c) Cout[(size_t)(row0 + ty + r * TY) * D + tx + c * G::TX] = acc[r][c];
     }
     __syncthreads();
 }
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kLargeThreads, 1) large_kernel(const FusedPara
     constexpr int DD = G::DD;
 
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_code, s_second;
+    __shared__ int s_code;
     unsigned char *panels = smem;
     Real *gam = (Real *)(smem + large_panel_bytes<Real, D>());
     const int tid = threadIdx.x, nb = p.n_basis;
@@ -411,56 +411,102 @@ __global__ void __launch_bounds__(kLargeThreads, 1) large_kernel(const FusedPara
     __threadfence();
     __syncthreads();
 
-    // pairwise tree over blocks in FP64 (second arrival multiplies right * left); the product runs
-    // through this block's scratch, viewed as FP64 matrices
-    double2 *wsd = (double2 *)((unsigned char *)scratch + (size_t)blockIdx.x * kLargeSlots * DD * sizeof(C));
-    int idx = blockIdx.x, n = gridDim.x, level = 0, toff = 0;
-    while (n > 1) {
-        const int parent = idx >> 1;
-        if ((idx | 1) < n) {
-            if (tid == 0) s_second = (atomicAdd(&p.tickets[toff + parent], 1u) != 0u);
-            __syncthreads();
-            if (!s_second) return;
-            if (tid == 0) p.tickets[toff + parent] = 0u;
-            __threadfence();
-            double2 *gL = p.partials + (size_t)((idx & ~1) << level) * DD;
-            const double2 *gR = p.partials + (size_t)((idx | 1) << level) * DD;
-            double2 *L2 = wsd, *R2 = wsd + DD;
-            for (int e = tid; e < DD; e += kLargeThreads) {
-                L2[e] = __ldcg(gL + e);
-                R2[e] = __ldcg(gR + e);
+    // the pairwise tree over the block partials runs in tree_level_kernel launches
+}
+
+// One level of the pairwise tree over block partials (Sec. 2.2) for large D:
+// out[i] = in[2i+1] * in[2i] (the later partial on the left), an odd last
+// partial is carried.  Storage is FP64; the products are computed in Real
+// (FP64 for the top levels, FP32 below them in the FP32 modes).  Each block
+// computes one 32 x 32 tile of one product, so a level spreads over the GPU.
+// The last level (one output) also writes U_out and snapshots the statistics.
+template <typename Real, int D>
+__global__ void __launch_bounds__(256) tree_level_kernel(const double2 *__restrict__ in, int n_in,
+                                                         double2 *__restrict__ out, const FusedParams p) {
+    using C = typename Cx<Real>::T;
+    constexpr int T = 32, KP = 16;
+    __shared__ C As[T][KP + 1], Bs[KP][T + 1];
+    const int tiles = D / T;
+    const int ti = blockIdx.x / tiles, tj = blockIdx.x % tiles, pair = blockIdx.y;
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+    const size_t DD = (size_t)D * D;
+    const bool has_pair = 2 * pair + 1 < n_in;
+    const double2 *L = in + (size_t)(2 * pair) * DD;      // earlier
+    const double2 *R = in + (size_t)(2 * pair + 1) * DD;  // later
+    double2 *O = out + (size_t)pair * DD;
+    C acc[2][2];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) acc[r][c] = Cx<Real>::make(0, 0);
+    if (has_pair) {
+        for (int k0 = 0; k0 < D; k0 += KP) {
+            for (int e = threadIdx.x; e < T * KP; e += blockDim.x) {
+                const int r = e / KP, k = e % KP;
+                const double2 a = R[(size_t)(ti * T + r) * D + k0 + k];
+                As[r][k] = Cx<Real>::make((Real)a.x, (Real)a.y);
+                const int kb = e / T, cb = e % T;
+                const double2 b = L[(size_t)(k0 + kb) * D + tj * T + cb];
+                Bs[kb][cb] = Cx<Real>::make((Real)b.x, (Real)b.y);
             }
             __syncthreads();
-            cta_mm<double, D>(R2, L2, gL, panels);
-            __threadfence();
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                const C a0 = As[ty][k], a1 = As[ty + 16][k];
+                const C b0 = Bs[k][tx], b1 = Bs[k][tx + 16];
+                cfma(acc[0][0], a0, b0);
+                cfma(acc[0][1], a0, b1);
+                cfma(acc[1][0], a1, b0);
+                cfma(acc[1][1], a1, b1);
+            }
             __syncthreads();
         }
-        idx = parent;
-        n = (n + 1) >> 1;
-        toff += n;
-        ++level;
     }
-
-    const int d = p.d_out;
-    for (int e = tid; e < d * d; e += kLargeThreads) {
-        const double2 v = __ldcg(p.partials + (e / d) * D + (e % d));
-        if (p.out_c128) ((double2 *)p.U_out)[e] = v;
-        else ((float2 *)p.U_out)[e] = make_float2((float)v.x, (float)v.y);
-    }
-    if (tid == 0) {
-        __threadfence();
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int i = ti * T + ty + 16 * r, j = tj * T + tx + 16 * c;
+            const double2 v = has_pair ? make_double2((double)acc[r][c].x, (double)acc[r][c].y)
+                                       : L[(size_t)i * D + j];
+            O[(size_t)i * D + j] = v;
+            if (gridDim.y == 1 && n_in <= 2) {  // last level: the propagator itself
+                const int d = p.d_out;
+                if (i < d && j < d) {
+                    if (p.out_c128) ((double2 *)p.U_out)[i * d + j] = v;
+                    else ((float2 *)p.U_out)[i * d + j] = make_float2((float)v.x, (float)v.y);
+                }
+            }
+        }
+    if (gridDim.y == 1 && n_in <= 2 && blockIdx.x == 0 && threadIdx.x == 0) {
         for (int i = 0; i < 4; ++i) p.counters[4 + i] = atomicExch(&p.counters[i], 0ull);
         p.status[1] = atomicExch(&p.status[0], 0u);
     }
 }
 
+// Forward kernel, then the tree levels: FP64 products for the top three levels (and everywhere in
+// FP64 mode), Real products below.  The per-block scratch doubles as the second tree buffer.
 template <typename Real, int D, int INTEG, bool TC = false>
 cudaError_t launch_large(const FusedParams &p, void *scratch, int grid, size_t smem, cudaStream_t st) {
     auto k = large_kernel<Real, D, INTEG, TC>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, kLargeThreads, smem, st>>>(p, scratch);
-    return cudaGetLastError();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    double2 *bufs[2] = {p.partials, (double2 *)scratch};
+    int cur = 0, n = grid;
+    do {
+        const int n_out = (n + 1) / 2;
+        const dim3 g((D / 32) * (D / 32), n_out);
+        if (std::is_same<Real, double>::value || n <= 8)
+            tree_level_kernel<double, D><<<g, 256, 0, st>>>(bufs[cur], n, bufs[cur ^ 1], p);
+        else
+            tree_level_kernel<float, D><<<g, 256, 0, st>>>(bufs[cur], n, bufs[cur ^ 1], p);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        cur ^= 1;
+        n = n_out;
+    } while (n > 1);
+    return cudaSuccess;
 }
 
 }  // namespace pm
