@@ -255,10 +255,18 @@ __device__ void cta_mm_tc(const float2 *__restrict__ A, const float2 *__restrict
                     split_tf32(w1.y, bih[1], bil[1]);
 #pragma unroll
                     for (int i = 0; i < MT; ++i) {
-                        mma3(accr[i][j], arh[i], arl[i], brh, brl);  // + Re A Re B
-                        mma3(accr[i][j], nih[i], nil[i], bih, bil);  // - Im A Im B
-                        mma3(acci[i][j], arh[i], arl[i], bih, bil);  // + Re A Im B
-                        mma3(acci[i][j], aih[i], ail[i], brh, brl);  // + Im A Re B
+                        // each k8 step accumulates in fresh MMA registers; the running sums are
+                        // kept with round-to-nearest FP32 adds (the MMA accumulator truncates)
+                        float tr[4] = {0.f, 0.f, 0.f, 0.f}, ti[4] = {0.f, 0.f, 0.f, 0.f};
+                        mma3(tr, arh[i], arl[i], brh, brl);  // + Re A Re B
+                        mma3(tr, nih[i], nil[i], bih, bil);  // - Im A Im B
+                        mma3(ti, arh[i], arl[i], bih, bil);  // + Re A Im B
+                        mma3(ti, aih[i], ail[i], brh, brl);  // + Im A Re B
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) {
+                            accr[i][j][v] = __fadd_rn(accr[i][j][v], tr[v]);
+                            acci[i][j][v] = __fadd_rn(acci[i][j][v], ti[v]);
+                        }
                     }
                 }
             }
