@@ -115,7 +115,13 @@ typedef enum {
        workspace cap); leaves longer than a sub-chunk are re-computed from checkpoints */
     PARAMENT_OPT_GRAD_SUBCHUNK = 8,
     /* gradient: cap in MiB on the per-slice prefix buffer of the adjoint sweep (default 4096) */
-    PARAMENT_OPT_WORKSPACE_MB = 9
+    PARAMENT_OPT_WORKSPACE_MB = 9,
+    /* batched: target slices per leaf (0 = default 64) */
+    PARAMENT_OPT_BATCH_LEAF_STEPS = 10,
+    /* batched: work items per SM (0 = default 4) */
+    PARAMENT_OPT_BATCH_ITEMS_PER_SM = 11,
+    /* batched: 1 (default) = capture set-up and launch in a CUDA graph and replay it; 0 = launch directly */
+    PARAMENT_OPT_BATCH_GRAPH = 12
 } parament_option;
 
 /* per-call diagnostics of the most recent propagate (see parament_get_stats) */
@@ -214,6 +220,47 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec);
  */
 int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, void *grad_out, void *U_out,
                             parament_precision prec);
+
+/* One problem of a batched call; all pointers are device memory owned by the caller. */
+typedef struct {
+    int dim;            /* d, 1..128 */
+    int n_ctrl;         /* K, 0..16 */
+    const void *H0;     /* d x d, dtype of the call */
+    const void *Hk;     /* K x d x d (may be NULL when K = 0) */
+    const void *c;      /* K x S real samples, cdtype of the call, S as for set_controls */
+    int64_t n_steps;    /* N >= 0 */
+    double dt;          /* slice duration */
+    void *U_out;        /* d x d result, dtype of the call */
+} parament_instance;
+
+/*
+ * Propagate many independent problems of uneven dimension and step count in
+ * one persistent kernel launch (the paper propagates one problem per call;
+ * batching many is an extension).  Every instance is cut into work items by
+ * its cost (d^3 N); one block per SM takes items from an atomic queue,
+ * largest first, and runs the body that fits the instance's dimension;
+ * instances combine their pieces through their own pairwise arrival trees.
+ * The set-up (all bases) and the launch are captured in a CUDA graph that is
+ * replayed while the instance shapes stay the same (option
+ * PARAMENT_OPT_BATCH_GRAPH; the context must have a non-default stream).
+ * cdtype must match prec (F64 with FP64, F32 with FP32 and FP32_TC_TF32X3).
+ * Basis matrices are not pruned and Hermiticity is not checked.  Returns
+ * without waiting.  Contexts keep the batch plan, so the same context must not
+ * run two batches concurrently.
+ */
+int parament_propagate_batched(parament_ctx *ctx, const parament_instance *inst, int n_inst, parament_dtype dtype,
+                               parament_real_dtype cdtype, parament_integrator integrator, parament_precision prec);
+
+/*
+ * Autotuner of the batched launch: times the batch for every pair of
+ * (target slices per leaf in {32, 64, 128, 256}) x (work items per SM in
+ * {2, 4, 8}), keeps the fastest in the context options
+ * PARAMENT_OPT_BATCH_LEAF_STEPS / PARAMENT_OPT_BATCH_ITEMS_PER_SM and reports
+ * it (and its time in ms) through the optional outputs.  Waits for the GPU.
+ */
+int parament_batch_autotune(parament_ctx *ctx, const parament_instance *inst, int n_inst, parament_dtype dtype,
+                            parament_real_dtype cdtype, parament_integrator integrator, parament_precision prec,
+                            int *best_leaf_steps, int *best_items_per_sm, double *best_ms);
 
 /* Diagnostics of the latest propagate; waits for the stream. */
 int parament_get_stats(parament_ctx *ctx, parament_stats *out);

@@ -58,6 +58,9 @@ PARAMENT_OPT_EXTRA_SQUARINGS = 5
 PARAMENT_OPT_HERMITIAN_TOL_E12 = 7
 PARAMENT_OPT_GRAD_SUBCHUNK = 8
 PARAMENT_OPT_WORKSPACE_MB = 9
+PARAMENT_OPT_BATCH_LEAF_STEPS = 10
+PARAMENT_OPT_BATCH_ITEMS_PER_SM = 11
+PARAMENT_OPT_BATCH_GRAPH = 12
 
 PARAMENT_DEV_NONFINITE_NORM = 0x1
 PARAMENT_DEV_NORM_CAPPED = 0x2
@@ -90,6 +93,19 @@ class parament_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_ if not name.startswith("reserved")}
 
 
+class parament_instance(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("n_ctrl", ctypes.c_int),
+        ("H0", ctypes.c_void_p),
+        ("Hk", ctypes.c_void_p),
+        ("c", ctypes.c_void_p),
+        ("n_steps", ctypes.c_int64),
+        ("dt", ctypes.c_double),
+        ("U_out", ctypes.c_void_p),
+    ]
+
+
 _vp = ctypes.c_void_p
 _SIGS = {
     "parament_version": ([], ctypes.c_int),
@@ -110,6 +126,11 @@ _SIGS = {
     "parament_propagate_noalloc": ([ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp,
                                     ctypes.c_int, ctypes.c_int64, ctypes.c_double, _vp, ctypes.c_int, _vp],
                                    ctypes.c_int),
+    "parament_propagate_batched": ([_vp, ctypes.POINTER(parament_instance), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_int], ctypes.c_int),
+    "parament_batch_autotune": ([_vp, ctypes.POINTER(parament_instance), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "parament_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "parament_last_error": ([_vp], ctypes.c_char_p),
 }
@@ -216,6 +237,27 @@ def parament_propagate_noalloc(dim: int, n_ctrl: int, H0_ptr: int, Hk_ptr: int |
                                            U_ptr, int(prec), stream or None))
 
 
+def _instances(inst):
+    arr = (parament_instance * max(len(inst), 1))()
+    for i, q in enumerate(inst):
+        arr[i] = q
+    return arr
+
+
+def parament_propagate_batched(ctx, inst: list, dtype: int, cdtype: int, integrator: int, prec: int) -> None:
+    arr = _instances(inst)
+    _check(_lib.parament_propagate_batched(ctx, arr, len(inst), int(dtype), int(cdtype), int(integrator),
+                                           int(prec)), ctx)
+
+
+def parament_batch_autotune(ctx, inst: list, dtype: int, cdtype: int, integrator: int, prec: int):
+    arr = _instances(inst)
+    l, i, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(_lib.parament_batch_autotune(ctx, arr, len(inst), int(dtype), int(cdtype), int(integrator), int(prec),
+                                        ctypes.byref(l), ctypes.byref(i), ctypes.byref(ms)), ctx)
+    return l.value, i.value, ms.value
+
+
 def raw_call(name: str, *args) -> int:
     """Call a C entry point directly and return its status (for tests of the error paths)."""
     return getattr(_lib, name)(*args)
@@ -312,6 +354,41 @@ class Propagator:
         loss = parament_propagate_grad(self.ctx, V.data_ptr(), grad.data_ptr(), U.data_ptr() if want_U else None,
                                        PRECISIONS[prec])
         return (loss, grad, U) if want_U else (loss, grad)
+
+    def batch(self, problems, prec: str = "fp32", integrator: str = "midpoint"):
+        """Device-resident tensors and instance records for a batched call.
+
+        ``problems``: iterable of (H0, Hk, c, dt, n_steps).  Returns (instances, keep, outputs); ``keep``
+        holds the tensors the records point to.
+        """
+        torch = self._torch
+        cdt = torch.complex128 if prec == "fp64" else torch.complex64
+        rdt = torch.float64 if prec == "fp64" else torch.float32
+        inst, keep, outs = [], [], []
+        for (H0, Hk, c, dt, n) in problems:
+            H0t = torch.as_tensor(H0).to(cdt).to(self.device).contiguous()
+            d = H0t.shape[-1]
+            Hkt = torch.as_tensor(Hk).to(cdt).to(self.device).reshape(-1, d, d).contiguous()
+            ct = torch.as_tensor(c).to(rdt).to(self.device).contiguous()
+            U = torch.empty(d, d, dtype=cdt, device=self.device)
+            keep += [H0t, Hkt, ct]
+            outs.append(U)
+            inst.append(parament_instance(d, Hkt.shape[0], H0t.data_ptr(), Hkt.data_ptr() if Hkt.numel() else None,
+                                          ct.data_ptr() if ct.numel() else None, int(n), float(dt), U.data_ptr()))
+        return inst, keep, outs
+
+    def propagate_batched(self, inst, prec: str = "fp32", integrator: str = "midpoint"):
+        torch = self._torch
+        self._sync_stream()
+        parament_propagate_batched(self.ctx, inst, PARAMENT_C128 if prec == "fp64" else PARAMENT_C64,
+                                   PARAMENT_F64 if prec == "fp64" else PARAMENT_F32, INTEGRATORS[integrator],
+                                   PRECISIONS[prec])
+
+    def batch_autotune(self, inst, prec: str = "fp32", integrator: str = "midpoint"):
+        self._sync_stream()
+        return parament_batch_autotune(self.ctx, inst, PARAMENT_C128 if prec == "fp64" else PARAMENT_C64,
+                                       PARAMENT_F64 if prec == "fp64" else PARAMENT_F32, INTEGRATORS[integrator],
+                                       PRECISIONS[prec])
 
     def stats(self) -> dict:
         return parament_get_stats(self.ctx)

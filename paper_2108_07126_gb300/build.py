@@ -33,6 +33,12 @@ SOURCES = [
     "pm_large_d32.cu",
     "pm_large_d64.cu",
     "pm_large_d128.cu",
+    "pm_batched_fm.cu",
+    "pm_batched_fm_tc.cu",
+    "pm_batched_dm.cu",
+    "pm_batched_fg.cu",
+    "pm_batched_fg_tc.cu",
+    "pm_batched_dg.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

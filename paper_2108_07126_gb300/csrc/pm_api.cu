@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "../../include/parament.h"
+#include "pm_batched.cuh"
 #include "pm_common.cuh"
 #include "pm_grad.cuh"
 
@@ -37,6 +38,19 @@ PM_DECL_L(32)
 PM_DECL_L(64)
 PM_DECL_L(128)
 #undef PM_DECL_L
+cudaError_t batch_basis_launch(int, int, const BatchInst *, const int2 *, int, int, double2 *, void *, double *,
+                               cudaStream_t);
+#define PM_DECL_B(v)                                                                                     \
+    cudaError_t batched_launch_##v(const BatchItem *, int, unsigned *, const FusedParams *, unsigned char *, \
+                                   size_t, int, size_t, cudaStream_t);                                   \
+    int batched_blocks_per_sm_##v(size_t);
+PM_DECL_B(fm)
+PM_DECL_B(fm_tc)
+PM_DECL_B(dm)
+PM_DECL_B(fg)
+PM_DECL_B(fg_tc)
+PM_DECL_B(dg)
+#undef PM_DECL_B
 }  // namespace pm
 
 using namespace pm;
@@ -69,6 +83,18 @@ struct parament_ctx {
     Workspace hraw, full, packed64, packed32, bnorm, partials, tickets, counters, status, check;
     Workspace ctrl_copy, ctrl_conv, uout, bmax, cpacked64, cpacked32, cbnorm;
     Workspace gv, gvdag, gleaf, gblock, gbpin, gpin, gz, gpbuf, gckpt, ggrad, lscratch;
+    // batched plan
+    Workspace bparams, binsts, btable, bitems, bfull, bpacked, bnorms, bpartials, btickets, bcounters, bstatus,
+        bqueue, bscratch;
+    std::vector<int64_t> bkey;
+    std::vector<int> b_nblk;               // work items per instance in the current plan
+    std::vector<FusedParams> bparams_up;  // last uploaded parameter block
+    std::vector<BatchInst> binsts_up;
+    int b_n_items = 0, b_n_mats = 0, b_grid = 0, b_variant = -1, b_fp64 = 0, b_c128 = 0, b_magnus = 0, b_ninst = 0;
+    size_t b_smem = 0, b_stride = 0;
+    cudaGraphExec_t b_exec = nullptr;
+    bool last_batched = false;
+    int64_t opt_batch_leaf = 0, opt_batch_items = 0, opt_batch_graph = 1;
     int nb_eff = 0;
     std::vector<short> slot_of;
 
@@ -537,7 +563,11 @@ int parament_destroy(parament_ctx *ctx) {
                             &ctx->partials, &ctx->tickets, &ctx->counters, &ctx->status, &ctx->check,
                             &ctx->ctrl_copy, &ctx->ctrl_conv, &ctx->uout, &ctx->bmax, &ctx->cpacked64,
                             &ctx->cpacked32, &ctx->cbnorm, &ctx->gv, &ctx->gvdag, &ctx->gleaf, &ctx->gblock,
-                            &ctx->gbpin, &ctx->gpin, &ctx->gz, &ctx->gpbuf, &ctx->gckpt, &ctx->ggrad, &ctx->lscratch};
+                            &ctx->gbpin, &ctx->gpin, &ctx->gz, &ctx->gpbuf, &ctx->gckpt, &ctx->ggrad, &ctx->lscratch,
+                            &ctx->bparams, &ctx->binsts, &ctx->btable, &ctx->bitems, &ctx->bfull, &ctx->bpacked,
+                            &ctx->bnorms, &ctx->bpartials, &ctx->btickets, &ctx->bcounters, &ctx->bstatus,
+                            &ctx->bqueue, &ctx->bscratch};
+        if (ctx->b_exec) cudaGraphExecDestroy(ctx->b_exec);
         for (Workspace *w : all) ws_free(*w);
     }
     delete ctx;
@@ -1056,6 +1086,17 @@ int parament_set_option(parament_ctx *ctx, int key, int64_t value) {
             if (value < 1) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "workspace cap must be >= 1 MiB");
             ctx->opt_workspace_mb = value;
             return PARAMENT_OK;
+        case PARAMENT_OPT_BATCH_LEAF_STEPS:
+            if (value < 0 || value > (1 << 20)) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "leaf steps in [0, 2^20]");
+            ctx->opt_batch_leaf = value;
+            return PARAMENT_OK;
+        case PARAMENT_OPT_BATCH_ITEMS_PER_SM:
+            if (value < 0 || value > 64) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "items per SM in [0, 64]");
+            ctx->opt_batch_items = value;
+            return PARAMENT_OK;
+        case PARAMENT_OPT_BATCH_GRAPH:
+            ctx->opt_batch_graph = value != 0;
+            return PARAMENT_OK;
     }
     return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown option key %d", key);
 }
@@ -1071,6 +1112,9 @@ int parament_get_option(const parament_ctx *ctx, int key, int64_t *value) {
         case PARAMENT_OPT_HERMITIAN_TOL_E12: *value = ctx->opt_herm_tol; return PARAMENT_OK;
         case PARAMENT_OPT_GRAD_SUBCHUNK: *value = ctx->opt_grad_subchunk; return PARAMENT_OK;
         case PARAMENT_OPT_WORKSPACE_MB: *value = ctx->opt_workspace_mb; return PARAMENT_OK;
+        case PARAMENT_OPT_BATCH_LEAF_STEPS: *value = ctx->opt_batch_leaf; return PARAMENT_OK;
+        case PARAMENT_OPT_BATCH_ITEMS_PER_SM: *value = ctx->opt_batch_items; return PARAMENT_OK;
+        case PARAMENT_OPT_BATCH_GRAPH: *value = ctx->opt_batch_graph; return PARAMENT_OK;
     }
     return PARAMENT_ERR_INVALID_VALUE;
 }
@@ -1111,3 +1155,340 @@ cudaError_t basis_build(const void *raw, int c128, int d, int Dp, int K, int mag
 }
 
 }  // namespace pm
+
+// ------------------------------------------------------------------ batched propagation
+
+namespace {
+
+cudaError_t batched_launch(int variant, const BatchItem *items, int n_items, unsigned *queue,
+                           const FusedParams *params, unsigned char *scratch, size_t stride, int grid, size_t smem,
+                           cudaStream_t st) {
+    switch (variant) {
+        case 0: return batched_launch_fm(items, n_items, queue, params, scratch, stride, grid, smem, st);
+        case 1: return batched_launch_fm_tc(items, n_items, queue, params, scratch, stride, grid, smem, st);
+        case 2: return batched_launch_dm(items, n_items, queue, params, scratch, stride, grid, smem, st);
+        case 3: return batched_launch_fg(items, n_items, queue, params, scratch, stride, grid, smem, st);
+        case 4: return batched_launch_fg_tc(items, n_items, queue, params, scratch, stride, grid, smem, st);
+        case 5: return batched_launch_dg(items, n_items, queue, params, scratch, stride, grid, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int batched_occupancy(int variant, size_t smem) {
+    switch (variant) {
+        case 0: return batched_blocks_per_sm_fm(smem);
+        case 1: return batched_blocks_per_sm_fm_tc(smem);
+        case 2: return batched_blocks_per_sm_dm(smem);
+        case 3: return batched_blocks_per_sm_fg(smem);
+        case 4: return batched_blocks_per_sm_fg_tc(smem);
+        case 5: return batched_blocks_per_sm_dg(smem);
+    }
+    return 0;
+}
+
+// Build (when the shapes change) and enqueue one batched propagation.
+int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_dtype dtype,
+              parament_real_dtype cdtype, parament_integrator integ, parament_precision prec) {
+    if (n < 0 || (n > 0 && !inst)) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "bad instance list");
+    if (dtype != PARAMENT_C64 && dtype != PARAMENT_C128)
+        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown dtype %d", (int)dtype);
+    if (integ != PARAMENT_MIDPOINT && integ != PARAMENT_MAGNUS4_GL2)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "batched propagation supports midpoint and GL4 Magnus");
+    if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32 && prec != PARAMENT_PREC_FP32_TC_TF32X3)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "batched precision must be FP64, FP32 or FP32_TC_TF32X3");
+    const int fp64 = prec == PARAMENT_PREC_FP64, tc = prec == PARAMENT_PREC_FP32_TC_TF32X3;
+    if ((cdtype == PARAMENT_F64) != (fp64 != 0))
+        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "control dtype must match the precision in batched calls");
+    const int magnus = integ != PARAMENT_MIDPOINT;
+    const int variant = (magnus ? 3 : 0) + (fp64 ? 2 : (tc ? 1 : 0));
+    ctx->last_batched = true;
+    if (n == 0) return PARAMENT_OK;
+    for (int i = 0; i < n; ++i) {
+        const parament_instance &q = inst[i];
+        if (q.dim < 1 || q.dim > kMaxDim || q.n_ctrl < 0 || q.n_ctrl > kMaxControls || q.n_steps < 0 ||
+            q.n_steps > (int64_t)0x7fffffff || !std::isfinite(q.dt))
+            return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "instance %d: bad sizes", i);
+        const int64_t S = samples_for(q.n_steps, integ);
+        if (!q.H0 || !q.U_out || (q.n_ctrl > 0 && !q.Hk) || (q.n_ctrl > 0 && S > 0 && !q.c))
+            return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "instance %d: null pointer", i);
+        if (!is_device_ptr(q.H0) || !is_device_ptr(q.U_out) || (q.n_ctrl > 0 && !is_device_ptr(q.Hk)) ||
+            (q.n_ctrl > 0 && S > 0 && !is_device_ptr(q.c)))
+            return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "instance %d: batched calls take device pointers", i);
+    }
+    const int leaf_steps = ctx->opt_batch_leaf > 0 ? (int)ctx->opt_batch_leaf : 64;
+    const int items_per_sm = ctx->opt_batch_items > 0 ? (int)ctx->opt_batch_items : 4;
+    const size_t csz = fp64 ? 16 : 8, rsz = fp64 ? 8 : 4;
+
+    std::vector<int64_t> key = {n, dtype, cdtype, integ, prec, leaf_steps, items_per_sm};
+    for (int i = 0; i < n; ++i) {
+        key.push_back(inst[i].dim);
+        key.push_back(inst[i].n_ctrl);
+        key.push_back(inst[i].n_steps);
+    }
+    std::vector<int> Dp(n), nbs(n), nblk(n);
+    std::vector<size_t> full_off(n), packed_off(n), norm_off(n), part_off(n), tick_off(n);
+    if (key != ctx->bkey) {
+        if (ctx->b_exec) {
+            cudaGraphExecDestroy(ctx->b_exec);
+            ctx->b_exec = nullptr;
+        }
+        ctx->bkey.clear();
+        // cost model: d^3 N per instance; items sized to (total cost) / (items_per_sm * #SMs)
+        double total = 0.0;
+        for (int i = 0; i < n; ++i) {
+            Dp[i] = pad_dim(inst[i].dim);
+            nbs[i] = n_basis_for(inst[i].n_ctrl, integ);
+            total += std::pow((double)Dp[i], 3) * std::max<int64_t>(inst[i].n_steps, 1);
+        }
+        const double target = total / std::max(1, items_per_sm * ctx->sm_count);
+        size_t nf = 0, np = 0, nn = 0, npart = 0, ntick = 0;
+        size_t smem = 0, stride = 0;
+        int n_mats = 0;
+        std::vector<BatchItem> items;
+        std::vector<double> icost;
+        for (int i = 0; i < n; ++i) {
+            const int64_t N = inst[i].n_steps;
+            const double cost = std::pow((double)Dp[i], 3) * std::max<int64_t>(N, 1);
+            int64_t nb_cap;
+            if (Dp[i] <= kMaxSmallDim) {
+                nb_cap = std::max<int64_t>(1, N / ((int64_t)8 * fused_gpw(Dp[i], fp64) * leaf_steps));
+                smem = std::max(smem, fused_smem(Dp[i], fp64, nbs[i], 8));
+            } else {
+                nb_cap = std::max<int64_t>(1, N / leaf_steps);
+                smem = std::max(smem, large_smem(Dp[i], fp64, nbs[i]));
+                stride = std::max(stride, (size_t)6 * Dp[i] * Dp[i] * csz);
+            }
+            nblk[i] = (int)std::min<int64_t>({nb_cap, (int64_t)std::ceil(cost / std::max(target, 1.0)), 1024});
+            nblk[i] = std::max(nblk[i], 1);
+            full_off[i] = nf;
+            packed_off[i] = np;
+            norm_off[i] = nn;
+            part_off[i] = npart;
+            tick_off[i] = ntick;
+            nf += (size_t)nbs[i] * Dp[i] * Dp[i];
+            np += (size_t)nbs[i] * Dp[i] * Dp[i];
+            nn += nbs[i];
+            npart += (size_t)nblk[i] * Dp[i] * Dp[i];
+            ntick += 2 * (size_t)nblk[i] + 2;
+            n_mats += nbs[i];
+            for (int b = 0; b < nblk[i]; ++b) {
+                items.push_back({i, b, nblk[i], Dp[i]});
+                icost.push_back(cost / nblk[i]);
+            }
+        }
+        if (smem > ctx->smem_optin)
+            return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "batch needs %zu B shared memory per block", smem);
+        std::vector<int> order(items.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return icost[a] > icost[b]; });
+        std::vector<BatchItem> sorted(items.size());
+        for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+        std::vector<int2> table;
+        for (int i = 0; i < n; ++i)
+            for (int e = 0; e < nbs[i]; ++e) table.push_back(make_int2(i, e));
+        const int bps = batched_occupancy(variant, smem);
+        if (bps <= 0) return set_err(ctx, PARAMENT_ERR_CUDA, "batched occupancy query failed (%zu B)", smem);
+        const int grid = bps * ctx->sm_count;
+        int st;
+        if ((st = ws_reserve(ctx, ctx->bparams, (size_t)n * sizeof(FusedParams)))) return st;
+        if ((st = ws_reserve(ctx, ctx->binsts, (size_t)n * sizeof(BatchInst)))) return st;
+        if ((st = ws_reserve(ctx, ctx->btable, table.size() * sizeof(int2)))) return st;
+        if ((st = ws_reserve(ctx, ctx->bitems, sorted.size() * sizeof(BatchItem)))) return st;
+        if ((st = ws_reserve(ctx, ctx->bfull, nf * sizeof(double2)))) return st;
+        if ((st = ws_reserve(ctx, ctx->bpacked, np * rsz))) return st;
+        if ((st = ws_reserve(ctx, ctx->bnorms, nn * sizeof(double)))) return st;
+        if ((st = ws_reserve(ctx, ctx->bpartials, npart * sizeof(double2)))) return st;
+        if ((st = ws_reserve(ctx, ctx->btickets, ntick * sizeof(unsigned)))) return st;
+        if ((st = ws_reserve(ctx, ctx->bcounters, (size_t)n * 8 * sizeof(unsigned long long)))) return st;
+        if ((st = ws_reserve(ctx, ctx->bstatus, (size_t)n * 2 * sizeof(unsigned)))) return st;
+        if ((st = ws_reserve(ctx, ctx->bqueue, 16))) return st;
+        if ((st = ws_reserve(ctx, ctx->bscratch, std::max<size_t>(stride, 16) * grid))) return st;
+        PM_CUDA(cudaMemcpy(ctx->btable.ptr, table.data(), table.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        PM_CUDA(cudaMemcpy(ctx->bitems.ptr, sorted.data(), sorted.size() * sizeof(BatchItem), cudaMemcpyHostToDevice));
+        PM_CUDA(cudaMemset(ctx->btickets.ptr, 0, ntick * sizeof(unsigned)));
+        PM_CUDA(cudaMemset(ctx->bcounters.ptr, 0, (size_t)n * 8 * sizeof(unsigned long long)));
+        PM_CUDA(cudaMemset(ctx->bstatus.ptr, 0, (size_t)n * 2 * sizeof(unsigned)));
+        ctx->b_n_items = (int)sorted.size();
+        ctx->b_n_mats = n_mats;
+        ctx->b_grid = grid;
+        ctx->b_smem = smem;
+        ctx->b_stride = std::max<size_t>(stride, 16);
+        ctx->b_variant = variant;
+        ctx->b_fp64 = fp64;
+        ctx->b_c128 = dtype == PARAMENT_C128;
+        ctx->b_magnus = magnus;
+        ctx->b_ninst = n;
+        ctx->b_nblk = nblk;
+        ctx->bparams_up.clear();
+        ctx->binsts_up.clear();
+        ctx->bkey = key;
+    } else {
+        size_t nf = 0, np = 0, nn = 0, npart = 0, ntick = 0;
+        for (int i = 0; i < n; ++i) {
+            Dp[i] = pad_dim(inst[i].dim);
+            nbs[i] = n_basis_for(inst[i].n_ctrl, integ);
+            full_off[i] = nf;
+            packed_off[i] = np;
+            norm_off[i] = nn;
+            part_off[i] = npart;
+            tick_off[i] = ntick;
+            nf += (size_t)nbs[i] * Dp[i] * Dp[i];
+            np += (size_t)nbs[i] * Dp[i] * Dp[i];
+            nn += nbs[i];
+        }
+    }
+
+    // per-instance parameters (pointers may change between calls)
+    const std::vector<int> &nblk_of = ctx->b_nblk;
+    FusedParams base;
+    std::memset(&base, 0, sizeof(base));
+    build_classes(fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24), (int)ctx->opt_degree, base);
+    std::vector<FusedParams> params(n, base);
+    std::vector<BatchInst> insts(n);
+    size_t npart = 0, ntick = 0;
+    for (int i = 0; i < n; ++i) {
+        const parament_instance &q = inst[i];
+        FusedParams &p = params[i];
+        p.ctrl = q.c;
+        p.S = samples_for(q.n_steps, integ);
+        p.n_steps = q.n_steps;
+        p.K = q.n_ctrl;
+        p.n_basis = nbs[i];
+        p.n_coef = nbs[i];
+        for (int e = 0; e < kMaxBasis; ++e) p.slot_of[e] = (short)(e < nbs[i] ? e : -1);
+        p.d_out = q.dim;
+        p.out_c128 = dtype == PARAMENT_C128;
+        p.dt = q.dt;
+        p.packed = (const char *)ctx->bpacked.ptr + packed_off[i] * rsz;
+        p.bnorm1 = (const double *)ctx->bnorms.ptr + norm_off[i];
+        p.partials = (double2 *)ctx->bpartials.ptr + npart;
+        p.tickets = (unsigned *)ctx->btickets.ptr + ntick;
+        p.U_out = q.U_out;
+        p.counters = (unsigned long long *)ctx->bcounters.ptr + (size_t)i * 8;
+        p.status = (unsigned *)ctx->bstatus.ptr + (size_t)i * 2;
+        p.extra_squarings = (int)ctx->opt_extra_sq;
+        npart += (size_t)nblk_of[i] * Dp[i] * Dp[i];
+        ntick += 2 * (size_t)nblk_of[i] + 2;
+        insts[i] = BatchInst{q.H0, q.Hk, q.dim, Dp[i], q.n_ctrl, nbs[i], full_off[i], packed_off[i], norm_off[i]};
+    }
+    if (ctx->bparams_up.size() != params.size() ||
+        std::memcmp(ctx->bparams_up.data(), params.data(), params.size() * sizeof(FusedParams)) != 0) {
+        PM_CUDA(cudaMemcpyAsync(ctx->bparams.ptr, params.data(), params.size() * sizeof(FusedParams),
+                                cudaMemcpyHostToDevice, ctx->stream));
+        ctx->bparams_up = params;
+    }
+    if (ctx->binsts_up.size() != insts.size() ||
+        std::memcmp(ctx->binsts_up.data(), insts.data(), insts.size() * sizeof(BatchInst)) != 0) {
+        PM_CUDA(cudaMemcpyAsync(ctx->binsts.ptr, insts.data(), insts.size() * sizeof(BatchInst),
+                                cudaMemcpyHostToDevice, ctx->stream));
+        ctx->binsts_up = insts;
+    }
+
+    auto enqueue = [&]() -> cudaError_t {
+        cudaError_t e = batch_basis_launch(ctx->b_c128, ctx->b_fp64, (const BatchInst *)ctx->binsts.ptr,
+                                           (const int2 *)ctx->btable.ptr, ctx->b_n_mats, ctx->b_magnus,
+                                           (double2 *)ctx->bfull.ptr, ctx->bpacked.ptr, (double *)ctx->bnorms.ptr,
+                                           ctx->stream);
+        if (e != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(ctx->bqueue.ptr, 0, sizeof(unsigned), ctx->stream)) != cudaSuccess) return e;
+        return batched_launch(ctx->b_variant, (const BatchItem *)ctx->bitems.ptr, ctx->b_n_items,
+                              (unsigned *)ctx->bqueue.ptr, (const FusedParams *)ctx->bparams.ptr,
+                              (unsigned char *)ctx->bscratch.ptr, ctx->b_stride, ctx->b_grid, ctx->b_smem,
+                              ctx->stream);
+    };
+    if (ctx->opt_batch_graph && ctx->stream != nullptr) {
+        if (!ctx->b_exec) {
+            cudaGraph_t graph = nullptr;
+            PM_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue();
+            cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &graph);
+            if (e != cudaSuccess || e2 != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                return set_err(ctx, PARAMENT_ERR_CUDA, "graph capture failed: %s",
+                               cudaGetErrorString(e != cudaSuccess ? e : e2));
+            }
+            cudaError_t e3 = cudaGraphInstantiate(&ctx->b_exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e3 != cudaSuccess) {
+                ctx->b_exec = nullptr;
+                cudaGetLastError();
+                return set_err(ctx, PARAMENT_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e3));
+            }
+        }
+        PM_CUDA(cudaGraphLaunch(ctx->b_exec, ctx->stream));
+    } else {
+        PM_CUDA(enqueue());
+    }
+    int64_t tot = 0;
+    for (int i = 0; i < n; ++i) tot += inst[i].n_steps;
+    ctx->last = parament_stats{};
+    ctx->last.n_steps = tot;
+    ctx->last.grid_blocks = ctx->b_grid;
+    ctx->last.block_threads = 256;
+    ctx->last.leaves = ctx->b_n_items;
+    ctx->last.kernel_ms = -1.0;
+    return PARAMENT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int parament_propagate_batched(parament_ctx *ctx, const parament_instance *inst, int n_inst, parament_dtype dtype,
+                               parament_real_dtype cdtype, parament_integrator integrator, parament_precision prec) {
+    if (!ctx) return PARAMENT_ERR_INVALID_VALUE;
+    ctx->err.clear();
+    DeviceGuard guard(ctx->device);
+    return batch_run(ctx, inst, n_inst, dtype, cdtype, integrator, prec);
+}
+
+int parament_batch_autotune(parament_ctx *ctx, const parament_instance *inst, int n_inst, parament_dtype dtype,
+                            parament_real_dtype cdtype, parament_integrator integrator, parament_precision prec,
+                            int *best_leaf_steps, int *best_items_per_sm, double *best_ms) {
+    if (!ctx) return PARAMENT_ERR_INVALID_VALUE;
+    ctx->err.clear();
+    DeviceGuard guard(ctx->device);
+    const int leafs[] = {32, 64, 128, 256}, items[] = {2, 4, 8};
+    cudaEvent_t a, b;
+    PM_CUDA(cudaEventCreate(&a));
+    PM_CUDA(cudaEventCreate(&b));
+    double best = 1e300;
+    int bl = 64, bi = 4;
+    int st = PARAMENT_OK;
+    for (int l : leafs) {
+        for (int it : items) {
+            ctx->opt_batch_leaf = l;
+            ctx->opt_batch_items = it;
+            if ((st = batch_run(ctx, inst, n_inst, dtype, cdtype, integrator, prec))) break;  // warm-up + plan
+            float ms_sum = 0.f;
+            for (int r = 0; r < 3 && st == PARAMENT_OK; ++r) {
+                cudaEventRecord(a, ctx->stream);
+                st = batch_run(ctx, inst, n_inst, dtype, cdtype, integrator, prec);
+                cudaEventRecord(b, ctx->stream);
+                cudaEventSynchronize(b);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, a, b);
+                ms_sum += ms;
+            }
+            if (st) break;
+            if (ms_sum / 3.0 < best) {
+                best = ms_sum / 3.0;
+                bl = l;
+                bi = it;
+            }
+        }
+        if (st) break;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st) return st;
+    ctx->opt_batch_leaf = bl;
+    ctx->opt_batch_items = bi;
+    if (best_leaf_steps) *best_leaf_steps = bl;
+    if (best_items_per_sm) *best_items_per_sm = bi;
+    if (best_ms) *best_ms = best;
+    return PARAMENT_OK;
+}
+
+}  // extern "C"

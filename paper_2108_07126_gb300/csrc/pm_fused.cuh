@@ -257,14 +257,16 @@ template <> __device__ __forceinline__ void ld4<double>(const double *p, double 
     o[0] = a.x; o[1] = a.y; o[2] = b.x; o[3] = b.y;
 }
 
+// The whole propagation of one problem, executed by thread block `blk` of the
+// `nblk` blocks assigned to it (the grid of fused_small_kernel, or the blocks
+// of one instance of the batched kernel).  smem: the dynamic shared memory.
 template <typename Real, int D, int INTEG>
-__global__ void __launch_bounds__(256, 1) fused_small_kernel(const FusedParams p) {
+__device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nblk, unsigned char *smem) {
     using G = Geo<Real, D>;
     using C = typename G::C;
     constexpr int LANES = G::LANES, GPW = G::GPW, TR = G::TR, TC = G::TC, LD = G::LD, DD = G::DD;
     constexpr int SLOT = G::SLOT, NCH = G::NCH, PS = G::PS;
 
-    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_second;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
@@ -290,8 +292,8 @@ __global__ void __launch_bounds__(256, 1) fused_small_kernel(const FusedParams p
     }
 
     // ---- leaf of this group
-    const int64_t n_leaves = (int64_t)gridDim.x * W * GPW;
-    const int64_t leaf = ((int64_t)blockIdx.x * W + warp) * GPW + g;
+    const int64_t n_leaves = (int64_t)nblk * W * GPW;
+    const int64_t leaf = ((int64_t)blk * W + warp) * GPW + g;
     const int64_t j0 = p.n_steps * leaf / n_leaves;
     const int len = (int)(p.n_steps * (leaf + 1) / n_leaves - j0);
     const int wlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
@@ -514,8 +516,8 @@ __global__ void __launch_bounds__(256, 1) fused_small_kernel(const FusedParams p
     // ---- block partial in FP64 to global memory
     {
         const C *R0 = leaf_R(0);
-        double2 *dst = p.partials + (size_t)blockIdx.x * DD;
-        double2 *keep = p.block_out ? p.block_out + (size_t)blockIdx.x * DD : nullptr;
+        double2 *dst = p.partials + (size_t)blk * DD;
+        double2 *keep = p.block_out ? p.block_out + (size_t)blk * DD : nullptr;
         for (int t = tid; t < DD; t += blockDim.x) {
             const C v = R0[(t / D) * LD + (t % D)];
             dst[t] = make_double2((double)v.x, (double)v.y);
@@ -530,7 +532,7 @@ __global__ void __launch_bounds__(256, 1) fused_small_kernel(const FusedParams p
     double2 *bufL = (double2 *)(smem + boff);  // warp 0's workspace, free by now
     double2 *bufR = bufL + D * GD::LD;
     const int rb64 = (lane % GD::LANES) / GD::CBW, cb64 = (lane % GD::LANES) % GD::CBW;
-    int idx = blockIdx.x, n = gridDim.x, level = 0, toff = 0;
+    int idx = blk, n = nblk, level = 0, toff = 0;
     while (n > 1) {
         const int parent = idx >> 1;
         if ((idx | 1) < n) {
@@ -579,6 +581,12 @@ __global__ void __launch_bounds__(256, 1) fused_small_kernel(const FusedParams p
             p.status[1] = atomicExch(&p.status[0], 0u);
         }
     }
+}
+
+template <typename Real, int D, int INTEG>
+__global__ void __launch_bounds__(256, 1) fused_small_kernel(const FusedParams p) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    fused_body<Real, D, INTEG>(p, blockIdx.x, gridDim.x, smem);
 }
 
 // host-side launcher (explicitly instantiated per D in pm_fused_d*.cu)

@@ -295,25 +295,27 @@ __device__ __forceinline__ void large_mm(const typename Cx<Real>::T *A, const ty
     else cta_mm<Real, D>(A, B, Cout, panels);
 }
 
-template <typename Real, int D, int INTEG, bool TC = false>
-__global__ void __launch_bounds__(kLargeThreads, 1) large_kernel(const FusedParams p, void *scratch) {
+// One leaf (slices [N blk / nblk, N (blk + 1) / nblk)) of one problem by one
+// thread block; writes the leaf product to p.partials[blk] (FP64).
+// ws: this block's 6 D x D scratch matrices.
+template <typename Real, int D, int INTEG, bool TC>
+__device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Real>::T *ws, int blk, int nblk,
+                                           unsigned char *smem) {
     using G = LGeo<Real, D>;
     using C = typename G::C;
     constexpr int DD = G::DD;
 
-    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_code;
     unsigned char *panels = smem;
     Real *gam = (Real *)(smem + large_panel_bytes<Real, D>());
     const int tid = threadIdx.x, nb = p.n_basis;
 
-    C *ws = (C *)scratch + (size_t)blockIdx.x * kLargeSlots * DD;
     C *SX = ws, *SX2 = ws + DD, *SX3 = ws + 2 * DD, *SR = ws + 3 * DD, *P0 = ws + 4 * DD, *P1 = ws + 5 * DD;
     Real *gpk = (Real *)P0;  // packed exponent scratch, free once X is formed
     const Real *packed = (const Real *)p.packed;
 
-    const int64_t j0 = p.n_steps * blockIdx.x / gridDim.x;
-    const int len = (int)(p.n_steps * (blockIdx.x + 1) / gridDim.x - j0);
+    const int64_t j0 = p.n_steps * blk / nblk;
+    const int len = (int)(p.n_steps * (blk + 1) / nblk - j0);
 
     for (int e = tid; e < DD; e += kLargeThreads) SR[e] = Cx<Real>::make((e / D) == (e % D) ? Real(1) : Real(0), Real(0));
     unsigned flags = 0;
@@ -408,18 +410,74 @@ __global__ void __launch_bounds__(kLargeThreads, 1) large_kernel(const FusedPara
 
     // block partial (the leaf product) in FP64
     {
-        double2 *dst = p.partials + (size_t)blockIdx.x * DD;
+        double2 *dst = p.partials + (size_t)blk * DD;
         for (int e = tid; e < DD; e += kLargeThreads) {
             const C v = SR[e];
             dst[e] = make_double2((double)v.x, (double)v.y);
-            if (p.leaf_out) p.leaf_out[(size_t)blockIdx.x * DD + e] = dst[e];
-            if (p.block_out) p.block_out[(size_t)blockIdx.x * DD + e] = dst[e];
+            if (p.leaf_out) p.leaf_out[(size_t)blk * DD + e] = dst[e];
+            if (p.block_out) p.block_out[(size_t)blk * DD + e] = dst[e];
         }
     }
     __threadfence();
     __syncthreads();
+}
 
+template <typename Real, int D, int INTEG, bool TC = false>
+__global__ void __launch_bounds__(kLargeThreads, 1) large_kernel(const FusedParams p, void *scratch) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    using C = typename Cx<Real>::T;
+    large_body<Real, D, INTEG, TC>(p, (C *)scratch + (size_t)blockIdx.x * kLargeSlots * D * D, blockIdx.x, gridDim.x,
+                                   smem);
     // the pairwise tree over the block partials runs in tree_level_kernel launches
+}
+
+// Pairwise tree over the nblk leaf products of one problem without waiting:
+// the second block to reach a node multiplies (later on the left, FP64 products
+// through the block's scratch), the first one leaves; the root writes U_out and
+// snapshots the statistics.
+template <int D>
+__device__ void large_arrival_tree(const FusedParams &p, void *ws_bytes, int blk, int nblk, unsigned char *smem) {
+    constexpr int DD = D * D;
+    __shared__ int s_second;
+    const int tid = threadIdx.x;
+    double2 *L2 = (double2 *)ws_bytes, *R2 = L2 + DD;
+    int idx = blk, n = nblk, level = 0, toff = 0;
+    while (n > 1) {
+        const int parent = idx >> 1;
+        if ((idx | 1) < n) {
+            if (tid == 0) s_second = (atomicAdd(&p.tickets[toff + parent], 1u) != 0u);
+            __syncthreads();
+            if (!s_second) return;
+            if (tid == 0) p.tickets[toff + parent] = 0u;
+            __threadfence();
+            double2 *gL = p.partials + (size_t)((idx & ~1) << level) * DD;
+            const double2 *gR = p.partials + (size_t)((idx | 1) << level) * DD;
+            for (int e = tid; e < DD; e += kLargeThreads) {
+                L2[e] = __ldcg(gL + e);
+                R2[e] = __ldcg(gR + e);
+            }
+            __syncthreads();
+            cta_mm<double, D>(R2, L2, gL, smem);
+            __threadfence();
+            __syncthreads();
+        }
+        idx = parent;
+        n = (n + 1) >> 1;
+        toff += n;
+        ++level;
+    }
+    const int d = p.d_out;
+    for (int e = tid; e < d * d; e += kLargeThreads) {
+        const double2 v = __ldcg(p.partials + (e / d) * D + (e % d));
+        if (p.out_c128) ((double2 *)p.U_out)[e] = v;
+        else ((float2 *)p.U_out)[e] = make_float2((float)v.x, (float)v.y);
+    }
+    if (tid == 0) {
+        __threadfence();
+        for (int i = 0; i < 4; ++i) p.counters[4 + i] = atomicExch(&p.counters[i], 0ull);
+        p.status[1] = atomicExch(&p.status[0], 0u);
+    }
+    __syncthreads();
 }
 
 // One level of the pairwise tree over block partials (Sec. 2.2) for large D:

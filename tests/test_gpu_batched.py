@@ -1,0 +1,126 @@
+"""Batched propagation of instances with uneven dimension and step count (one persistent launch)."""
+
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2108_07126_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+U32 = 2.0 ** -24
+
+
+def tol32(d, n):
+    return 20.0 * U32 * max(d, 2) * math.sqrt(max(n, 1)) + 1e-6
+
+
+@pytest.fixture()
+def prop():
+    import torch
+
+    from paper_2108_07126_gb300.binding import Propagator
+
+    assert torch.cuda.is_available()
+    p = Propagator(0)
+    yield p
+    p.close()
+
+
+def mixed_batch(integrator="midpoint", seed=0):
+    rng = np.random.default_rng(seed)
+    shapes = [(2, 1, 0), (2, 2, 1), (3, 2, 777), (4, 3, 5000), (8, 2, 3001), (16, 4, 20000), (5, 1, 129),
+              (32, 2, 600), (64, 3, 300), (12, 2, 2048), (40, 2, 97), (16, 6, 1)]
+    probs = []
+    for i, (d, K, n) in enumerate(shapes):
+        probs.append(wl.random_problem(d, K, n, integrator, seed=int(rng.integers(1 << 30)), g_norm=0.3))
+    return probs
+
+
+def refs(probs, rounded=False):
+    out = []
+    for p in probs:
+        if rounded:
+            out.append(oracle.propagate(p.H0.astype(np.complex64).astype(np.complex128),
+                                        p.Hk.astype(np.complex64).astype(np.complex128),
+                                        p.c.astype(np.float32).astype(np.float64), p.dt, p.integrator))
+        else:
+            out.append(oracle.propagate(p.H0, p.Hk, p.c, p.dt, p.integrator))
+    return out
+
+
+@pytest.mark.parametrize("graph", [1, 0])
+@pytest.mark.parametrize("integrator", ["midpoint", "magnus4_gl2"])
+def test_batched_fp64_matches_oracle(prop, graph, integrator):
+    import torch
+
+    from paper_2108_07126_gb300 import binding as b
+
+    probs = mixed_batch(integrator, seed=1)
+    prop.set_option(b.PARAMENT_OPT_BATCH_GRAPH, graph)
+    inst, keep, outs = prop.batch([(p.H0, p.Hk, p.c, p.dt, p.n_steps) for p in probs], "fp64")
+    R = refs(probs)
+    for rep in range(2):  # the second call replays the captured graph
+        for U in outs:
+            U.fill_(float("nan"))
+        prop.propagate_batched(inst, "fp64", integrator)
+        torch.cuda.synchronize()
+        for p, U, r in zip(probs, outs, R):
+            assert np.max(np.abs(U.cpu().numpy() - r)) <= TOL64, (p.name, rep)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_tc_tf32x3"])
+def test_batched_fp32_matches_oracle(prop, prec):
+    import torch
+
+    probs = mixed_batch("midpoint", seed=2)
+    inst, keep, outs = prop.batch([(p.H0, p.Hk, p.c, p.dt, p.n_steps) for p in probs], prec)
+    prop.propagate_batched(inst, prec)
+    torch.cuda.synchronize()
+    for p, U, r in zip(probs, outs, refs(probs, rounded=True)):
+        err = np.max(np.abs(U.cpu().numpy().astype(np.complex128) - r))
+        assert err <= 2 * tol32(p.dim, p.n_steps), (p.name, err)
+
+
+def test_batched_matches_single_calls(prop):
+    """Same inputs through the batched and the per-instance entry points (FP64)."""
+    import torch
+
+    probs = mixed_batch("midpoint", seed=3)[:8]
+    inst, keep, outs = prop.batch([(p.H0, p.Hk, p.c, p.dt, p.n_steps) for p in probs], "fp64")
+    prop.propagate_batched(inst, "fp64")
+    torch.cuda.synchronize()
+    for p, U in zip(probs, outs):
+        prop.set_hamiltonians(torch.as_tensor(p.H0), torch.as_tensor(p.Hk), p.integrator)
+        prop.set_controls(torch.as_tensor(p.c), p.dt, p.n_steps)
+        Us = prop.propagate("fp64")
+        assert torch.max(torch.abs(Us - U)).item() <= 1e-12
+
+
+def test_batched_workload_sample_and_autotune(prop):
+    import torch
+
+    probs = wl.batched_instances(n_inst=24, n_max=2e4)
+    inst, keep, outs = prop.batch([(p.H0, p.Hk, p.c, p.dt, p.n_steps) for p in probs], "fp32")
+    leaf, items, ms = prop.batch_autotune(inst, "fp32")
+    assert leaf in (32, 64, 128, 256) and items in (2, 4, 8) and ms > 0
+    prop.propagate_batched(inst, "fp32")
+    torch.cuda.synchronize()
+    for p, U, r in zip(probs, outs, refs(probs, rounded=True)):
+        err = np.max(np.abs(U.cpu().numpy().astype(np.complex128) - r))
+        assert err <= 2 * tol32(p.dim, p.n_steps), (p.name, err)
+
+
+def test_batched_rejects_host_pointers(prop):
+    from paper_2108_07126_gb300 import binding as b
+
+    H = np.eye(2, dtype=np.complex64)
+    U = np.zeros((2, 2), np.complex64)
+    inst = [b.parament_instance(2, 0, H.ctypes.data, None, None, 4, 0.1, U.ctypes.data)]
+    with pytest.raises(b.ParamentError) as e:
+        b.parament_propagate_batched(prop.ctx, inst, b.PARAMENT_C64, b.PARAMENT_F32, b.PARAMENT_MIDPOINT,
+                                     b.PARAMENT_PREC_FP32)
+    assert e.value.status == b.PARAMENT_ERR_INVALID_VALUE
