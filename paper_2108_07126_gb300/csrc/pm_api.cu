@@ -88,6 +88,7 @@ struct parament_ctx {
         bqueue, bscratch;
     std::vector<int64_t> bkey;
     std::vector<int> b_nblk;               // work items per instance in the current plan
+    std::vector<int> b_warps;              // leaf-owning warps per block for each instance (D <= 16)
     std::vector<FusedParams> bparams_up;  // last uploaded parameter block
     std::vector<BatchInst> binsts_up;
     int b_n_items = 0, b_n_mats = 0, b_grid = 0, b_variant = -1, b_fp64 = 0, b_c128 = 0, b_magnus = 0, b_ninst = 0;
@@ -1225,7 +1226,7 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
         key.push_back(inst[i].n_ctrl);
         key.push_back(inst[i].n_steps);
     }
-    std::vector<int> Dp(n), nbs(n), nblk(n);
+    std::vector<int> Dp(n), nbs(n), nblk(n), warps_of(n, 8);
     std::vector<size_t> full_off(n), packed_off(n), norm_off(n), part_off(n), tick_off(n);
     if (key != ctx->bkey) {
         if (ctx->b_exec) {
@@ -1251,8 +1252,11 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
             const double cost = std::pow((double)Dp[i], 3) * std::max<int64_t>(N, 1);
             int64_t nb_cap;
             if (Dp[i] <= kMaxSmallDim) {
-                nb_cap = std::max<int64_t>(1, N / ((int64_t)8 * fused_gpw(Dp[i], fp64) * leaf_steps));
-                smem = std::max(smem, fused_smem(Dp[i], fp64, nbs[i], 8));
+                int w = 8;
+                while (w > 1 && fused_smem(Dp[i], fp64, nbs[i], w) > ctx->smem_optin) --w;
+                warps_of[i] = w;
+                nb_cap = std::max<int64_t>(1, N / ((int64_t)w * fused_gpw(Dp[i], fp64) * leaf_steps));
+                smem = std::max(smem, fused_smem(Dp[i], fp64, nbs[i], w));
             } else {
                 nb_cap = std::max<int64_t>(1, N / leaf_steps);
                 smem = std::max(smem, large_smem(Dp[i], fp64, nbs[i]));
@@ -1319,6 +1323,7 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
         ctx->b_magnus = magnus;
         ctx->b_ninst = n;
         ctx->b_nblk = nblk;
+        ctx->b_warps = warps_of;
         ctx->bparams_up.clear();
         ctx->binsts_up.clear();
         ctx->bkey = key;
@@ -1367,6 +1372,7 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
         p.counters = (unsigned long long *)ctx->bcounters.ptr + (size_t)i * 8;
         p.status = (unsigned *)ctx->bstatus.ptr + (size_t)i * 2;
         p.extra_squarings = (int)ctx->opt_extra_sq;
+        p.warps = ctx->b_warps[i];
         npart += (size_t)nblk_of[i] * Dp[i] * Dp[i];
         ntick += 2 * (size_t)nblk_of[i] + 2;
         insts[i] = BatchInst{q.H0, q.Hk, q.dim, Dp[i], q.n_ctrl, nbs[i], full_off[i], packed_off[i], norm_off[i]};

@@ -70,6 +70,7 @@ struct FusedParams {
     unsigned long long *counters;
     unsigned *status;
     int extra_squarings;
+    int warps;                 // warps of a block that own leaves (0 = all; the others only join the barriers)
     int n_cls;
     double cls_cap[kMaxClasses];
     int cls_code[kMaxClasses];

@@ -269,7 +269,9 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
 
     __shared__ int s_second;
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, W = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int W = (p.warps > 0 && p.warps < (int)(blockDim.x >> 5)) ? p.warps : (int)(blockDim.x >> 5);
+    const bool active_warp = warp < W;  // warps beyond W own no leaf and no shared workspace
     const int g = lane / LANES, gl = lane % LANES;
     const int rb = gl / G::CBW, cb = gl % G::CBW;
     const int nb = p.n_basis;
@@ -294,12 +296,12 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
     // ---- leaf of this group
     const int64_t n_leaves = (int64_t)nblk * W * GPW;
     const int64_t leaf = ((int64_t)blk * W + warp) * GPW + g;
-    const int64_t j0 = p.n_steps * leaf / n_leaves;
-    const int len = (int)(p.n_steps * (leaf + 1) / n_leaves - j0);
+    const int64_t j0 = active_warp ? p.n_steps * leaf / n_leaves : 0;
+    const int len = active_warp ? (int)(p.n_steps * (leaf + 1) / n_leaves - j0) : 0;
     const int wlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
 
     // R = I
-    {
+    if (active_warp) {
         C t[TR][TC];
 #pragma unroll
         for (int r = 0; r < TR; ++r)
@@ -479,7 +481,7 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
     }
 
     // ---- optional: every leaf product in FP64 (checkpoints of the adjoint pass)
-    if (p.leaf_out) {
+    if (p.leaf_out && active_warp) {
         double2 *dst = p.leaf_out + (size_t)leaf * DD;
         for (int t = gl; t < DD; t += LANES) {
             const C v = SR[(t / D) * LD + (t % D)];
