@@ -258,6 +258,71 @@ def secondary_workloads(torch, b, wl, dev, flush, steps=10, warmup=3):
             "loss_abs_err_vs_oracle": abs(loss - l_ref),
             "grad_max_rel_err_vs_oracle": float(np.max(np.abs(g - g_ref)) / np.max(np.abs(g_ref))),
             "launches_per_step": 5, "timing": "host wall clock incl. the loss read-back"}
+    # ---- batched sweep: 256 instances, d in {2..64}, N log-uniform in [1e3, 1e5]
+    probs = wl.batched_instances()
+    total_steps = sum(p.n_steps for p in probs)
+    inst32, keep32, outs32 = prop.batch([(p.H0, p.Hk, p.c, p.dt, p.n_steps) for p in probs], "fp32")
+    leaf, items, tune_ms = prop.batch_autotune(inst32, "fp32")
+    per = time_launches(torch, lambda: prop.propagate_batched(inst32, "fp32"), 5, 2, flush)
+    ms32 = statistics.mean(per)
+    inst_tc, keep_tc, outs_tc = prop.batch([(p.H0, p.Hk, p.c, p.dt, p.n_steps) for p in probs], "fp32_tc_tf32x3")
+    prop.batch_autotune(inst_tc, "fp32_tc_tf32x3")
+    per_tc = time_launches(torch, lambda: prop.propagate_batched(inst_tc, "fp32_tc_tf32x3"), 5, 2, flush)
+    ms_tc = statistics.mean(per_tc)
+    # plain FP64 GPU path: one propagate per instance
+    U64 = []
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record()
+    for p in probs:
+        prop.set_hamiltonians(torch.as_tensor(p.H0).to(dev), torch.as_tensor(p.Hk).to(dev), "midpoint")
+        prop.set_controls(torch.as_tensor(p.c).to(dev), p.dt, p.n_steps)
+        U64.append(prop.propagate("fp64"))
+    t1.record()
+    torch.cuda.synchronize()
+    ms64 = t0.elapsed_time(t1)
+    err32 = max(float(torch.max(torch.abs(a.to(torch.complex128) - b)).item()) for a, b in zip(outs32, U64))
+    err_tc = max(float(torch.max(torch.abs(a.to(torch.complex128) - b)).item()) for a, b in zip(outs_tc, U64))
+    out["batched_256_instances_d2to64"] = {
+        "total_steps": total_steps, "n_instances": len(probs),
+        "fp32_batched": {"steps_per_s": total_steps / (ms32 * 1e-3), "ms": ms32, "launches": 2,
+                         "autotuned": {"leaf_steps": leaf, "items_per_sm": items}, "cuda_graph": True,
+                         "max_abs_err_vs_fp64_gpu": err32},
+        "fp32_tc_tf32x3_batched": {"steps_per_s": total_steps / (ms_tc * 1e-3), "ms": ms_tc,
+                                   "max_abs_err_vs_fp64_gpu": err_tc},
+        "fp64_gpu_per_instance_loop": {"steps_per_s": total_steps / (ms64 * 1e-3), "ms": ms64,
+                                       "note": "set_hamiltonians + set_controls + propagate per instance, "
+                                               "the set-up synchronises"},
+        "speedup_fp32_batched_vs_fp64_loop": ms64 / ms32}
+    del keep32, keep_tc, outs32, outs_tc, U64
+
+    # ---- dense precision stress: d = 128, GL4, N = 2^16 (FP64 timed on 2^12 slices)
+    prob = wl.dense_stress()
+    small = wl.dense_stress(n_steps=1 << 12)
+    res = {}
+    for name, prb in (("full", prob), ("small", small)):
+        for prec in ("fp32", "fp32_tc_tf32x3") + (("fp64",) if name == "small" else ()):
+            cdt = torch.complex128 if prec == "fp64" else torch.complex64
+            rdt = torch.float64 if prec == "fp64" else torch.float32
+            prop.set_hamiltonians(torch.as_tensor(prb.H0).to(cdt), torch.as_tensor(prb.Hk).to(cdt), prb.integrator)
+            prop.set_controls(torch.as_tensor(prb.c).to(rdt).to(dev), prb.dt, prb.n_steps)
+            U = torch.empty(128, 128, dtype=cdt, device=dev)
+            per = time_launches(torch, lambda: prop.propagate(prec, out=U), 3 if prec != "fp64" else 1, 1, flush)
+            st = prop.stats()
+            res[(name, prec)] = (statistics.mean(per), U.cpu().numpy().astype(np.complex128), st)
+    U64s = res[("small", "fp64")][1]
+    d128 = {}
+    for prec in ("fp32", "fp32_tc_tf32x3"):
+        ms, _, st = res[("full", prec)]
+        fl = flops_per_launch(st)
+        d128[prec] = {"steps_per_s": prob.n_steps / (ms * 1e-3), "ms": ms, "algorithmic_tflops": fl / (ms * 1e-3) / 1e12,
+                      "max_abs_err_vs_fp64_gpu_N4096": float(np.max(np.abs(res[("small", prec)][1] - U64s)))}
+    ms, _, st = res[("small", "fp64")]
+    d128["fp64"] = {"steps_per_s": small.n_steps / (ms * 1e-3), "ms_N4096": ms,
+                    "algorithmic_tflops": flops_per_launch(st) / (ms * 1e-3) / 1e12}
+    d128["speedup_tf32x3_vs_fp64"] = d128["fp32_tc_tf32x3"]["steps_per_s"] / d128["fp64"]["steps_per_s"]
+    out["dense_stress_d128_magnus4_gl2_N65536"] = d128
     prop.close()
     return out
 
