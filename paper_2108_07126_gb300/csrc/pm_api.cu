@@ -7,8 +7,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/parament.h"
@@ -323,9 +326,73 @@ struct Cand {
 
 const int kDegrees[][3] = {{1, 1, 1}, {2, 2, 1}, {4, 2, 2}, {6, 3, 2}, {9, 3, 3}, {12, 3, 4}};  // m, q, r
 
+struct ClassTable {
+    int n_cls;
+    double cap[kMaxClasses];
+    int code[kMaxClasses];
+    double coef_d[kMaxDegree + 1];
+    float coef_f[kMaxDegree + 1];
+};
+
+int build_classes_uncached(double u, int force_m, FusedParams &p, int shift);
+
+// The table depends only on (u, force_m, shift); it is computed once per process (a few
+// hundred root solves) so that a propagation call costs microseconds on the host.
+int build_classes(double u, int force_m, FusedParams &p, int shift = 0) {
+    static std::mutex mu;
+    static std::map<std::tuple<double, int, int>, ClassTable> memo;
+    const auto key = std::make_tuple(u, force_m, shift);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = memo.find(key);
+        if (it != memo.end()) {
+            const ClassTable &t = it->second;
+            p.n_cls = t.n_cls;
+            std::memcpy(p.cls_cap, t.cap, sizeof(t.cap));
+            std::memcpy(p.cls_code, t.code, sizeof(t.code));
+            std::memcpy(p.coef_d, t.coef_d, sizeof(t.coef_d));
+            std::memcpy(p.coef_f, t.coef_f, sizeof(t.coef_f));
+            return p.n_cls;
+        }
+    }
+    const int n = build_classes_uncached(u, force_m, p, shift);
+    if (n > 0) {
+        ClassTable t;
+        t.n_cls = p.n_cls;
+        std::memcpy(t.cap, p.cls_cap, sizeof(t.cap));
+        std::memcpy(t.code, p.cls_code, sizeof(t.code));
+        std::memcpy(t.coef_d, p.coef_d, sizeof(t.coef_d));
+        std::memcpy(t.coef_f, p.coef_f, sizeof(t.coef_f));
+        std::lock_guard<std::mutex> lock(mu);
+        memo[key] = t;
+    }
+    return n;
+}
+
+// Occupancy queries are memoised per (device, kernel family, shape, shared memory).
+template <typename F>
+int memo_occupancy(int kind, int Dp, int fp64, int integ, int warps, size_t smem, int extra, F &&query) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, int, int, size_t, int>, int> memo;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, kind, Dp, fp64, integ, warps, smem, extra);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = memo.find(key);
+        if (it != memo.end()) return it->second;
+    }
+    const int v = query();
+    if (v > 0) {
+        std::lock_guard<std::mutex> lock(mu);
+        memo[key] = v;
+    }
+    return v;
+}
+
 // shift = 0: truncation bound of exp; shift = 1: of its Frechet derivative
 // (the derivative series loses one power: remainder ~ x^m / m! e^x).
-int build_classes(double u, int force_m, FusedParams &p, int shift = 0) {
+int build_classes_uncached(double u, int force_m, FusedParams &p, int shift) {
     std::vector<Cand> all;
     for (int s = 0; s <= 62; ++s) {
         for (const auto &dg : kDegrees) {
@@ -376,7 +443,7 @@ cudaError_t fused_dispatch(int Dp, int fp64, int integ, const FusedParams &p, in
     }
     return cudaErrorInvalidValue;
 }
-int fused_blocks_per_sm(int Dp, int fp64, int integ, int warps, size_t smem) {
+int fused_blocks_per_sm_uncached(int Dp, int fp64, int integ, int warps, size_t smem) {
     switch (Dp) {
         case 2: return fused_blocks_per_sm_d2(fp64, integ, warps, smem);
         case 4: return fused_blocks_per_sm_d4(fp64, integ, warps, smem);
@@ -384,6 +451,10 @@ int fused_blocks_per_sm(int Dp, int fp64, int integ, int warps, size_t smem) {
         case 16: return fused_blocks_per_sm_d16(fp64, integ, warps, smem);
     }
     return 0;
+}
+int fused_blocks_per_sm(int Dp, int fp64, int integ, int warps, size_t smem) {
+    return memo_occupancy(0, Dp, fp64, integ, warps, smem, 0,
+                          [&] { return fused_blocks_per_sm_uncached(Dp, fp64, integ, warps, smem); });
 }
 size_t fused_smem(int Dp, int fp64, int nb, int warps) {
     switch (Dp) {
@@ -431,13 +502,17 @@ cudaError_t large_dispatch(int Dp, int fp64, int integ, const FusedParams &p, vo
     }
     return cudaErrorInvalidValue;
 }
-int large_blocks_per_sm(int Dp, int fp64, int integ, size_t smem, int tc) {
+int large_blocks_per_sm_uncached(int Dp, int fp64, int integ, size_t smem, int tc) {
     switch (Dp) {
         case 32: return large_blocks_per_sm_d32(fp64, integ, smem, tc);
         case 64: return large_blocks_per_sm_d64(fp64, integ, smem, tc);
         case 128: return large_blocks_per_sm_d128(fp64, integ, smem, tc);
     }
     return 0;
+}
+int large_blocks_per_sm(int Dp, int fp64, int integ, size_t smem, int tc) {
+    return memo_occupancy(1, Dp, fp64, integ, 8, smem, tc,
+                          [&] { return large_blocks_per_sm_uncached(Dp, fp64, integ, smem, tc); });
 }
 size_t large_smem(int Dp, int fp64, int nb) {
     switch (Dp) {
