@@ -37,6 +37,10 @@ UNIT = "time steps/s"
 FP32_PEAK_TFLOPS_NOTE = "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz max SM clock"
 SM_COUNT, FP32_LANES, FP64_FMA_PER_SM_CLK = 152, 128, 2
 L2_FLUSH_BYTES = 256 << 20
+# dram__bytes_read.sum + dram__bytes_write.sum of fused_small_kernel<float, 16, GL4> from one ncu capture of
+# 2^18 slices (16 921 344 + 0 bytes), scaled per slice: the traffic is the control samples, linear in N
+TRAFFIC_BYTES_PER_SLICE = 16921344 / 262144
+TRAFFIC_NOTE = "ncu capture of 2^18 slices (16.92 MB) scaled to the launch; algorithmic 64 B per slice"
 
 
 def parse_args():
@@ -433,7 +437,8 @@ def run_ours(args):
                    "tree_products": st32["tree_products"], "max_degree": st32["max_degree"],
                    "max_squarings": st32["max_squarings"], "flops_per_launch": fl32},
         "roofline": {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
-                     "traffic": None, "peak_note": FP32_PEAK_TFLOPS_NOTE},
+                     "traffic": TRAFFIC_BYTES_PER_SLICE * N, "traffic_note": TRAFFIC_NOTE,
+                     "peak_note": FP32_PEAK_TFLOPS_NOTE},
         "cpu_baseline": cpu,
         "e2e": {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(c_host.numel() * 4),
                 "d2h_bytes_per_step": int(U_host.nbytes)},
