@@ -328,6 +328,21 @@ int parament_propagate_noalloc(int dim, int n_ctrl, const void *H0, const void *
                                parament_integrator integrator, const void *c, parament_real_dtype cdtype,
                                int64_t n_steps, double dt, void *U_out, parament_precision prec, void *cuda_stream);
 
+/*
+ * Chebyshev exponential (Sec. 2.1): the largest half-width beta of the spectral
+ * interval [-beta, beta] for which the truncation bound of Eq. error_chebychev,
+ * eps = 4 (exp(1 - y^2) y)^(m+1), y = 2 beta / (4m + 4), stays below u (with
+ * u = 2^-24 / 2^-53 this is Table 1).  Host-only; -1 for m outside [1, 48].
+ */
+double parament_chebyshev_theta(int m, double u);
+
+/* Smallest degree m <= 48 whose Chebyshev bound covers half-width beta at u; -1 if none. */
+int parament_chebyshev_degree(double half_width, double u);
+
+/* Bessel functions J_0(x) .. J_n(x), x >= 0, n <= 48 (Miller's backward recurrence), the
+   Chebyshev coefficients a_k = (-i)^k J_k(beta) of Sec. 2.1; host-only, the kernels use the same code. */
+int parament_bessel_j(int n, double x, double *out);
+
 /* Static text for a status code. */
 const char *parament_status_string(int status);
 

@@ -131,6 +131,9 @@ _SIGS = {
     "parament_batch_autotune": ([_vp, ctypes.POINTER(parament_instance), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "parament_chebyshev_theta": ([ctypes.c_int, ctypes.c_double], ctypes.c_double),
+    "parament_chebyshev_degree": ([ctypes.c_double, ctypes.c_double], ctypes.c_int),
+    "parament_bessel_j": ([ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "parament_status_string": ([ctypes.c_int], ctypes.c_char_p),
     "parament_last_error": ([_vp], ctypes.c_char_p),
 }
@@ -256,6 +259,20 @@ def parament_batch_autotune(ctx, inst: list, dtype: int, cdtype: int, integrator
     _check(_lib.parament_batch_autotune(ctx, arr, len(inst), int(dtype), int(cdtype), int(integrator), int(prec),
                                         ctypes.byref(l), ctypes.byref(i), ctypes.byref(ms)), ctx)
     return l.value, i.value, ms.value
+
+
+def parament_chebyshev_theta(m: int, u: float) -> float:
+    return _lib.parament_chebyshev_theta(int(m), float(u))
+
+
+def parament_chebyshev_degree(half_width: float, u: float) -> int:
+    return _lib.parament_chebyshev_degree(float(half_width), float(u))
+
+
+def parament_bessel_j(n: int, x: float) -> list:
+    out = (ctypes.c_double * (n + 1))()
+    _check(_lib.parament_bessel_j(int(n), float(x), out))
+    return list(out)
 
 
 def raw_call(name: str, *args) -> int:

@@ -16,6 +16,7 @@
 
 #include "../../include/parament.h"
 #include "pm_batched.cuh"
+#include "pm_cheb.cuh"
 #include "pm_common.cuh"
 #include "pm_grad.cuh"
 
@@ -230,6 +231,7 @@ __global__ void check_hermitian_kernel(const InT *raw, int d, int n_mat, unsigne
 // Basis B_e (FP64, padded to Dp): H0, H_k and, for the Magnus exponents,
 // i[H0, H_k] and i[H_a, H_b] (a < b), the effective control Hamiltonians of
 // Sec. 4, Eq. magnus_coeffs.
+// grid: (basis matrices, tiles of 256 entries)
 template <typename InT>
 __global__ void build_basis_kernel(const InT *raw, int d, int Dp, int K, int magnus, double2 *full) {
     const int e = blockIdx.x;
@@ -248,7 +250,7 @@ __global__ void build_basis_kernel(const InT *raw, int d, int Dp, int K, int mag
         }
     }
     (void)magnus;
-    for (int t = threadIdx.x; t < Dp * Dp; t += blockDim.x) {
+    for (int t = blockIdx.y * blockDim.x + threadIdx.x; t < Dp * Dp; t += gridDim.y * blockDim.x) {
         const int i = t / Dp, j = t % Dp;
         double2 v = make_double2(0.0, 0.0);
         if (i < d && j < d) {
@@ -587,6 +589,24 @@ int parament_taylor_choice(double norm_bound, double u, int force_m, int *m_out,
     return PARAMENT_OK;
 }
 
+double parament_chebyshev_theta(int m, double u) {
+    if (m < 1 || m > kMaxChebDegree || !(u > 0.0) || !(u < 1.0)) return -1.0;
+    return cheb_theta(m, u);
+}
+
+int parament_chebyshev_degree(double half_width, double u) {
+    if (!(half_width >= 0.0) || std::isinf(half_width) || !(u > 0.0) || !(u < 1.0)) return -1;
+    for (int m = 1; m <= kMaxChebDegree; ++m)
+        if (cheb_theta(m, u) >= half_width) return m;
+    return -1;
+}
+
+int parament_bessel_j(int n, double x, double *out) {
+    if (!out || n < 0 || n > kMaxChebDegree || !(x >= 0.0) || std::isinf(x)) return PARAMENT_ERR_INVALID_VALUE;
+    bessel_j_seq(x, n, out);
+    return PARAMENT_OK;
+}
+
 int parament_create(parament_ctx **out, int device, void *cuda_stream) {
     if (!out) return PARAMENT_ERR_INVALID_VALUE;
     *out = nullptr;
@@ -711,12 +731,13 @@ int parament_set_hamiltonians(parament_ctx *ctx, int dim, int n_ctrl, const void
     const int grid_cap = Dp <= kMaxSmallDim ? ctx->max_grid : 2 * ctx->sm_count;
     if ((st = ws_reserve(ctx, ctx->partials, (size_t)grid_cap * DD * sizeof(double2)))) return st;
     const int magnus = integrator != PARAMENT_MIDPOINT;
+    const dim3 bgrid(nb, (unsigned)std::max<size_t>(1, DD / 256));
     if (dtype == PARAMENT_C128)
-        build_basis_kernel<double2><<<nb, 256, 0, ctx->stream>>>((const double2 *)ctx->hraw.ptr, dim, Dp, n_ctrl,
-                                                                 magnus, (double2 *)ctx->full.ptr);
+        build_basis_kernel<double2><<<bgrid, 256, 0, ctx->stream>>>((const double2 *)ctx->hraw.ptr, dim, Dp, n_ctrl,
+                                                                    magnus, (double2 *)ctx->full.ptr);
     else
-        build_basis_kernel<float2><<<nb, 256, 0, ctx->stream>>>((const float2 *)ctx->hraw.ptr, dim, Dp, n_ctrl,
-                                                                magnus, (double2 *)ctx->full.ptr);
+        build_basis_kernel<float2><<<bgrid, 256, 0, ctx->stream>>>((const float2 *)ctx->hraw.ptr, dim, Dp, n_ctrl,
+                                                                   magnus, (double2 *)ctx->full.ptr);
     PM_CUDA(cudaGetLastError());
     if ((st = ws_reserve(ctx, ctx->bmax, nb * sizeof(double)))) return st;
     pack_basis_kernel<<<nb, 256, 0, ctx->stream>>>((const double2 *)ctx->full.ptr, Dp, (double *)ctx->packed64.ptr,
@@ -1220,10 +1241,11 @@ int fused_groups(int Dp, int fp64) { return fused_gpw(Dp, fp64); }
 
 cudaError_t basis_build(const void *raw, int c128, int d, int Dp, int K, int magnus, int nb, double2 *full,
                         double *p64, float *p32, double *bnorm, double *bmax, cudaStream_t st) {
+    const dim3 bgrid(nb, (unsigned)std::max(1, Dp * Dp / 256));
     if (c128)
-        build_basis_kernel<double2><<<nb, 256, 0, st>>>((const double2 *)raw, d, Dp, K, magnus, full);
+        build_basis_kernel<double2><<<bgrid, 256, 0, st>>>((const double2 *)raw, d, Dp, K, magnus, full);
     else
-        build_basis_kernel<float2><<<nb, 256, 0, st>>>((const float2 *)raw, d, Dp, K, magnus, full);
+        build_basis_kernel<float2><<<bgrid, 256, 0, st>>>((const float2 *)raw, d, Dp, K, magnus, full);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     pack_basis_kernel<<<nb, 256, 0, st>>>(full, Dp, p64, p32, bnorm, bmax);

@@ -132,3 +132,34 @@ def test_taylor_choice_forced_and_invalid():
         b.parament_taylor_choice(0.5, 2.0 ** -53, 5)
     with pytest.raises(b.ParamentError):
         b.parament_taylor_choice(float("nan"), 2.0 ** -53)
+
+
+def test_chebyshev_bound_reproduces_table1():
+    """Table 1 of Sec. 2.1 from the error bound of Eq. error_chebychev (printed to three digits)."""
+    import json
+
+    from paper_2108_07126_gb300 import binding as b
+
+    t = json.load(open(os.path.join(ROOT, "tests", "golden", "chebyshev_table1.json")))
+    for m, v32, v64 in zip(t["m_max"], t["fp32"], t["fp64"]):
+        th32 = b.parament_chebyshev_theta(m, 2.0 ** -24)
+        th64 = b.parament_chebyshev_theta(m, 2.0 ** -53)
+        assert abs(th32 - v32) <= 0.5e-3 + 1e-9, (m, th32, v32)
+        if m == 3:
+            assert abs(th64 - v64) <= 0.5e-4, (m, th64)  # printed as 2e-4
+        else:
+            assert abs(th64 - v64) <= 0.5e-3 + 1e-9, (m, th64, v64)
+        assert b.parament_chebyshev_degree(th32 * 0.999, 2.0 ** -24) <= m
+        assert b.parament_chebyshev_degree(th32 * 1.001, 2.0 ** -24) > m
+
+
+@pytest.mark.parametrize("x", [0.0, 1e-8, 0.3, 1.7, 4.45, 9.9, 25.0])
+def test_bessel_sequence_matches_scipy(x):
+    import scipy.special
+
+    from paper_2108_07126_gb300 import binding as b
+
+    n = 40
+    got = b.parament_bessel_j(n, x)
+    ref = scipy.special.jv(range(n + 1), x)
+    assert max(abs(g - r) for g, r in zip(got, ref)) <= 1e-14
