@@ -121,7 +121,12 @@ typedef enum {
     /* batched: work items per SM (0 = default 4) */
     PARAMENT_OPT_BATCH_ITEMS_PER_SM = 11,
     /* batched: 1 (default) = capture set-up and launch in a CUDA graph and replay it; 0 = launch directly */
-    PARAMENT_OPT_BATCH_GRAPH = 12
+    PARAMENT_OPT_BATCH_GRAPH = 12,
+    /* exponential of parament_propagate: 0 (default) = Taylor with scaling and squaring, degree per
+       slice; 1 = the paper's Chebyshev series (Sec. 2.1, Algorithm 1) with one spectral interval
+       [-beta, beta] for all slices (beta = largest per-slice norm bound, found on the device) and the
+       degree of Eq. error_chebychev; d <= 16 */
+    PARAMENT_OPT_EXP_METHOD = 13
 } parament_option;
 
 /* per-call diagnostics of the most recent propagate (see parament_get_stats) */

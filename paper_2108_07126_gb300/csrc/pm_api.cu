@@ -22,8 +22,8 @@
 
 namespace pm {
 #define PM_DECL_D(D)                                                                                     \
-    cudaError_t fused_dispatch_d##D(int, int, const FusedParams &, int, int, size_t, cudaStream_t);      \
-    int fused_blocks_per_sm_d##D(int, int, int, size_t);                                                 \
+    cudaError_t fused_dispatch_d##D(int, int, const FusedParams &, int, int, size_t, cudaStream_t, int); \
+    int fused_blocks_per_sm_d##D(int, int, int, size_t, int);                                            \
     size_t fused_smem_d##D(int, int, int);                                                               \
     int fused_groups_per_warp_d##D(int);                                                                 \
     cudaError_t grad_run_d##D(int, const ScanParams &, const GradParams &, int, int, size_t, cudaStream_t); \
@@ -100,6 +100,8 @@ struct parament_ctx {
     cudaGraphExec_t b_exec = nullptr;
     bool last_batched = false;
     int64_t opt_batch_leaf = 0, opt_batch_items = 0, opt_batch_graph = 1;
+    int64_t opt_exp_method = 0;
+    Workspace cheb;  // Chebyshev pre-pass: max norm bound, degree, 1/beta, coefficients
     int nb_eff = 0;
     std::vector<short> slot_of;
 
@@ -319,6 +321,77 @@ __global__ void convert_kernel(const From *src, To *dst, int64_t n) {
         dst[i] = (To)src[i];
 }
 
+// ------------------------------------------------------------------ Chebyshev pre-pass
+
+struct ChebTheta {
+    double t[kMaxChebDegree + 1];  // t[m] = largest half-width covered by degree m
+};
+
+// Largest per-slice bound nu_j = sum_e |gamma_e| ||B_e||_1 over all slices: the common
+// spectral half-width beta (the paper uses one alpha, beta for all slices, Sec. 3.2).
+template <typename Real, int INTEG>
+__global__ void cheb_bound_kernel(const FusedParams p, unsigned long long *numax, unsigned *status) {
+    Real gam[kMaxBasis];
+    double nu_max = 0.0;
+    bool bad = false;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < p.n_steps;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        slice_coefficients<Real, INTEG, 1>(p, j, true, gam);
+        double nu = 0.0;
+        for (int e = 0; e < p.n_basis; ++e) nu = fma(fabs((double)gam[e]), p.bnorm1[e], nu);
+        if (!(nu <= 1e300)) bad = true;
+        else nu_max = fmax(nu_max, nu);
+    }
+    for (int off = 16; off > 0; off >>= 1) nu_max = fmax(nu_max, __shfl_xor_sync(0xffffffffu, nu_max, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(numax, (unsigned long long)__double_as_longlong(nu_max));
+    if (bad) atomicOr(status, kDevNonfinite);
+}
+
+// Degree (smallest m whose bound covers beta; Sec. 2.1) and coefficients a_k = (-i)^k J_k(beta)
+template <typename C>
+__global__ void cheb_coef_kernel(const unsigned long long *numax, const ChebTheta th, int *m_out, double *inv_beta,
+                                 C *coef, unsigned *status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double beta = __longlong_as_double((long long)*numax);
+    int m = kMaxChebDegree;
+    bool capped = true;
+    for (int k = 1; k <= kMaxChebDegree; ++k)
+        if (th.t[k] >= beta) {
+            m = k;
+            capped = false;
+            break;
+        }
+    if (capped) atomicOr(status, kDevCapped);
+    double J[kMaxChebDegree + 1];
+    bessel_j_seq(beta, m, J);
+    for (int k = 0; k <= m; ++k) {
+        const double v = J[k];
+        double re = 0.0, im = 0.0;
+        switch (k & 3) {
+            case 0: re = v; break;
+            case 1: im = -v; break;
+            case 2: re = -v; break;
+            case 3: im = v; break;
+        }
+        coef[k].x = re;
+        coef[k].y = im;
+    }
+    *m_out = m;
+    *inv_beta = beta > 0.0 ? 1.0 / beta : 0.0;
+}
+
+const ChebTheta &cheb_theta_table(double u) {
+    static std::mutex mu;
+    static std::map<double, ChebTheta> memo;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = memo.find(u);
+    if (it != memo.end()) return it->second;
+    ChebTheta t;
+    t.t[0] = 0.0;
+    for (int m = 1; m <= kMaxChebDegree; ++m) t.t[m] = cheb_theta(m, u);
+    return memo.emplace(u, t).first->second;
+}
+
 // ------------------------------------------------------------------ Taylor classes
 
 struct Cand {
@@ -436,27 +509,27 @@ int build_classes_uncached(double u, int force_m, FusedParams &p, int shift) {
 }
 
 cudaError_t fused_dispatch(int Dp, int fp64, int integ, const FusedParams &p, int grid, int warps, size_t smem,
-                           cudaStream_t st) {
+                           cudaStream_t st, int cheb = 0) {
     switch (Dp) {
-        case 2: return fused_dispatch_d2(fp64, integ, p, grid, warps, smem, st);
-        case 4: return fused_dispatch_d4(fp64, integ, p, grid, warps, smem, st);
-        case 8: return fused_dispatch_d8(fp64, integ, p, grid, warps, smem, st);
-        case 16: return fused_dispatch_d16(fp64, integ, p, grid, warps, smem, st);
+        case 2: return fused_dispatch_d2(fp64, integ, p, grid, warps, smem, st, cheb);
+        case 4: return fused_dispatch_d4(fp64, integ, p, grid, warps, smem, st, cheb);
+        case 8: return fused_dispatch_d8(fp64, integ, p, grid, warps, smem, st, cheb);
+        case 16: return fused_dispatch_d16(fp64, integ, p, grid, warps, smem, st, cheb);
     }
     return cudaErrorInvalidValue;
 }
-int fused_blocks_per_sm_uncached(int Dp, int fp64, int integ, int warps, size_t smem) {
+int fused_blocks_per_sm_uncached(int Dp, int fp64, int integ, int warps, size_t smem, int cheb) {
     switch (Dp) {
-        case 2: return fused_blocks_per_sm_d2(fp64, integ, warps, smem);
-        case 4: return fused_blocks_per_sm_d4(fp64, integ, warps, smem);
-        case 8: return fused_blocks_per_sm_d8(fp64, integ, warps, smem);
-        case 16: return fused_blocks_per_sm_d16(fp64, integ, warps, smem);
+        case 2: return fused_blocks_per_sm_d2(fp64, integ, warps, smem, cheb);
+        case 4: return fused_blocks_per_sm_d4(fp64, integ, warps, smem, cheb);
+        case 8: return fused_blocks_per_sm_d8(fp64, integ, warps, smem, cheb);
+        case 16: return fused_blocks_per_sm_d16(fp64, integ, warps, smem, cheb);
     }
     return 0;
 }
-int fused_blocks_per_sm(int Dp, int fp64, int integ, int warps, size_t smem) {
-    return memo_occupancy(0, Dp, fp64, integ, warps, smem, 0,
-                          [&] { return fused_blocks_per_sm_uncached(Dp, fp64, integ, warps, smem); });
+int fused_blocks_per_sm(int Dp, int fp64, int integ, int warps, size_t smem, int cheb = 0) {
+    return memo_occupancy(0, Dp, fp64, integ, warps, smem, cheb,
+                          [&] { return fused_blocks_per_sm_uncached(Dp, fp64, integ, warps, smem, cheb); });
 }
 size_t fused_smem(int Dp, int fp64, int nb, int warps) {
     switch (Dp) {
@@ -662,7 +735,7 @@ int parament_destroy(parament_ctx *ctx) {
                             &ctx->gbpin, &ctx->gpin, &ctx->gz, &ctx->gpbuf, &ctx->gckpt, &ctx->ggrad, &ctx->lscratch,
                             &ctx->bparams, &ctx->binsts, &ctx->btable, &ctx->bitems, &ctx->bfull, &ctx->bpacked,
                             &ctx->bnorms, &ctx->bpartials, &ctx->btickets, &ctx->bcounters, &ctx->bstatus,
-                            &ctx->bqueue, &ctx->bscratch};
+                            &ctx->bqueue, &ctx->bscratch, &ctx->cheb};
         if (ctx->b_exec) cudaGraphExecDestroy(ctx->b_exec);
         for (Workspace *w : all) ws_free(*w);
     }
@@ -967,9 +1040,44 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) 
     FusedParams p;
     int grid = 0, warps = 0, lpb = 0;
     size_t smem = 0;
+    const int cheb = ctx->opt_exp_method == 1;
+    if (cheb && ctx->dpad > kMaxSmallDim)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "the Chebyshev exponential is built for d <= %d", kMaxSmallDim);
     int st = forward_setup(ctx, fp64, dst, p, grid, warps, smem, lpb, tc);
     if (st) return st;
-    PM_CUDA(forward_launch(ctx, fp64, p, grid, warps, smem, tc));
+    if (cheb) {
+        // common spectral half-width over all slices, then degree and coefficients, on the device
+        if ((st = ws_reserve(ctx, ctx->cheb, 1024))) return st;
+        unsigned char *cw = (unsigned char *)ctx->cheb.ptr;
+        unsigned long long *numax = (unsigned long long *)cw;
+        int *mptr = (int *)(cw + 8);
+        double *ibeta = (double *)(cw + 16);
+        void *coef = cw + 32;
+        PM_CUDA(cudaMemsetAsync(numax, 0, 8, ctx->stream));
+        const int bgrid = (int)std::max<int64_t>(1, std::min<int64_t>((ctx->n_steps + 255) / 256, 4 * ctx->sm_count));
+        const ChebTheta &th = cheb_theta_table(fp64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24));
+        const int ig = (int)ctx->integ;
+        if (fp64) {
+            if (ig == 0) cheb_bound_kernel<double, kMidpoint><<<bgrid, 256, 0, ctx->stream>>>(p, numax, p.status);
+            else if (ig == 1) cheb_bound_kernel<double, kGL2><<<bgrid, 256, 0, ctx->stream>>>(p, numax, p.status);
+            else cheb_bound_kernel<double, kSimpson><<<bgrid, 256, 0, ctx->stream>>>(p, numax, p.status);
+            cheb_coef_kernel<double2><<<1, 32, 0, ctx->stream>>>(numax, th, mptr, ibeta, (double2 *)coef, p.status);
+        } else {
+            if (ig == 0) cheb_bound_kernel<float, kMidpoint><<<bgrid, 256, 0, ctx->stream>>>(p, numax, p.status);
+            else if (ig == 1) cheb_bound_kernel<float, kGL2><<<bgrid, 256, 0, ctx->stream>>>(p, numax, p.status);
+            else cheb_bound_kernel<float, kSimpson><<<bgrid, 256, 0, ctx->stream>>>(p, numax, p.status);
+            cheb_coef_kernel<float2><<<1, 32, 0, ctx->stream>>>(numax, th, mptr, ibeta, (float2 *)coef, p.status);
+        }
+        PM_CUDA(cudaGetLastError());
+        p.cheb_m = mptr;
+        p.cheb_inv_beta = ibeta;
+        p.cheb_coef = coef;
+        if (fused_blocks_per_sm(ctx->dpad, fp64, ig, warps, smem, 1) <= 0)
+            return set_err(ctx, PARAMENT_ERR_CUDA, "occupancy query failed (Chebyshev kernel)");
+        PM_CUDA(fused_dispatch(ctx->dpad, fp64, ig, p, grid, warps, smem, ctx->stream, 1));
+    } else {
+        PM_CUDA(forward_launch(ctx, fp64, p, grid, warps, smem, tc));
+    }
     record_launch(ctx, ctx->nb_eff, grid, warps, lpb);
 
     if (host_out) {
@@ -1194,6 +1302,10 @@ int parament_set_option(parament_ctx *ctx, int key, int64_t value) {
         case PARAMENT_OPT_BATCH_GRAPH:
             ctx->opt_batch_graph = value != 0;
             return PARAMENT_OK;
+        case PARAMENT_OPT_EXP_METHOD:
+            if (value != 0 && value != 1) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "exp method is 0 or 1");
+            ctx->opt_exp_method = value;
+            return PARAMENT_OK;
     }
     return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown option key %d", key);
 }
@@ -1212,6 +1324,7 @@ int parament_get_option(const parament_ctx *ctx, int key, int64_t *value) {
         case PARAMENT_OPT_BATCH_LEAF_STEPS: *value = ctx->opt_batch_leaf; return PARAMENT_OK;
         case PARAMENT_OPT_BATCH_ITEMS_PER_SM: *value = ctx->opt_batch_items; return PARAMENT_OK;
         case PARAMENT_OPT_BATCH_GRAPH: *value = ctx->opt_batch_graph; return PARAMENT_OK;
+        case PARAMENT_OPT_EXP_METHOD: *value = ctx->opt_exp_method; return PARAMENT_OK;
     }
     return PARAMENT_ERR_INVALID_VALUE;
 }

@@ -71,6 +71,9 @@ struct FusedParams {
     unsigned *status;
     int extra_squarings;
     int warps;                 // warps of a block that own leaves (0 = all; the others only join the barriers)
+    const int *cheb_m;         // Chebyshev mode: degree, 1 / beta and coefficients (device, written by
+    const double *cheb_inv_beta;  //   cheb_coef_kernel)
+    const void *cheb_coef;     // Real complex [m + 1]: a_k = (-i)^k J_k(beta)
     int n_cls;
     double cls_cap[kMaxClasses];
     int cls_code[kMaxClasses];

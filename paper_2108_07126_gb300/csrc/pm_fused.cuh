@@ -260,7 +260,7 @@ template <> __device__ __forceinline__ void ld4<double>(const double *p, double 
 // The whole propagation of one problem, executed by thread block `blk` of the
 // `nblk` blocks assigned to it (the grid of fused_small_kernel, or the blocks
 // of one instance of the batched kernel).  smem: the dynamic shared memory.
-template <typename Real, int D, int INTEG>
+template <typename Real, int D, int INTEG, int EXPM = 0>
 __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nblk, unsigned char *smem) {
     using G = Geo<Real, D>;
     using C = typename G::C;
@@ -322,9 +322,13 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
             const bool act = (t0 + gl) < len;
             Real *gcol = gam + lane;
             slice_coefficients<Real, INTEG>(p, j0 + t0 + gl, act, gcol);
-            double nu = 0.0;
-            for (int e = 0; e < nb; ++e) nu = fma(fabs((double)gcol[e * 32]), bnorm[e], nu);
-            cls[lane] = find_class(p, nu, &flags);
+            if (EXPM == 0) {
+                double nu = 0.0;
+                for (int e = 0; e < nb; ++e) nu = fma(fabs((double)gcol[e * 32]), bnorm[e], nu);
+                cls[lane] = find_class(p, nu, &flags);
+            } else {
+                cls[lane] = 0;  // Chebyshev: one global degree, fixed before the launch
+            }
         }
         __syncwarp();
         const int nr = min(LANES, wlen - t0);
@@ -363,6 +367,80 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
                     }
             }
             __syncwarp();
+
+            if constexpr (EXPM == 1) {
+                // -- Chebyshev (Sec. 2.1, Algorithm 1): X = G / beta, D_k = a_k I + 2 X D_{k+1} - D_{k+2},
+                //    exp(-i G) ~ D_0 - D_2; one product per degree, then the leaf product
+                const Real ib = (Real)*p.cheb_inv_beta;
+                const int mch = *p.cheb_m;
+                const C *ak = (const C *)p.cheb_coef;
+                C dk1[TR][TC], dk2[TR][TC], U[TR][TC];
+#pragma unroll
+                for (int r = 0; r < TR; ++r)
+#pragma unroll
+                    for (int c = 0; c < TC; ++c) {
+                        const int i = rb + r * G::RBN, jj = G::col(cb, c);
+                        const Real a = gpk[i * PS + jj], b = gpk[jj * PS + i];
+                        const Real re = (i <= jj) ? a : b;
+                        const Real im = (i > jj) ? a : ((i < jj) ? -b : Real(0));
+                        U[r][c] = Cx<Real>::make(re * ib, im * ib);
+                    }
+                st_tile<Real, D>(S1, rb, cb, U);
+                {
+                    const C am = ak[mch];
+#pragma unroll
+                    for (int r = 0; r < TR; ++r)
+#pragma unroll
+                        for (int c = 0; c < TC; ++c) {
+                            const bool diag = (rb + r * G::RBN) == G::col(cb, c);
+                            dk1[r][c] = diag ? am : Cx<Real>::make(0, 0);
+                            dk2[r][c] = Cx<Real>::make(0, 0);
+                        }
+                }
+                __syncwarp();
+                for (int k = mch - 1; k >= 0; --k) {
+                    st_tile<Real, D>(S2, rb, cb, dk1);
+                    __syncwarp();
+                    C acc[TR][TC];
+                    mm_tile<Real, D>(S1, S2, rb, cb, acc);
+                    __syncwarp();
+                    const C a_k = ak[k];
+#pragma unroll
+                    for (int r = 0; r < TR; ++r)
+#pragma unroll
+                        for (int c = 0; c < TC; ++c) {
+                            const bool diag = (rb + r * G::RBN) == G::col(cb, c);
+                            C v = Cx<Real>::make(Real(2) * acc[r][c].x - dk2[r][c].x,
+                                                 Real(2) * acc[r][c].y - dk2[r][c].y);
+                            if (diag) {
+                                v.x += a_k.x;
+                                v.y += a_k.y;
+                            }
+                            if (k == 0) {
+                                U[r][c] = Cx<Real>::make(v.x - dk2[r][c].x, v.y - dk2[r][c].y);
+                            } else {
+                                dk2[r][c] = dk1[r][c];
+                                dk1[r][c] = v;
+                            }
+                        }
+                }
+                // leaf product R <- U_j R (skipped for padding slices, which would multiply by ~I)
+                st_tile<Real, D>(S2, rb, cb, U);
+                __syncwarp();
+                {
+                    C acc[TR][TC];
+                    mm_tile<Real, D>(S2, SR, rb, cb, acc);
+                    __syncwarp();
+                    if ((t0 + rr) < len) st_tile<Real, D>(SR, rb, cb, acc);
+                    __syncwarp();
+                }
+                if (gl == 0 && (t0 + rr) < len) {
+                    n_exp += (unsigned long long)mch;
+                    n_tree += 1;
+                    m_max = max(m_max, mch);
+                }
+                continue;
+            }
 
             // -- unpack the Hermitian G into A = -i G / 2^s at the lane's tile
             const Real sc = pow2neg<Real>(s);
@@ -585,26 +663,26 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
     }
 }
 
-template <typename Real, int D, int INTEG>
+template <typename Real, int D, int INTEG, int EXPM = 0>
 __global__ void __launch_bounds__(256, 1) fused_small_kernel(const FusedParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
-    fused_body<Real, D, INTEG>(p, blockIdx.x, gridDim.x, smem);
+    fused_body<Real, D, INTEG, EXPM>(p, blockIdx.x, gridDim.x, smem);
 }
 
 // host-side launcher (explicitly instantiated per D in pm_fused_d*.cu)
-template <typename Real, int D, int INTEG>
+template <typename Real, int D, int INTEG, int EXPM = 0>
 cudaError_t launch_fused(const FusedParams &p, int grid, int warps, size_t smem, cudaStream_t st) {
-    auto k = fused_small_kernel<Real, D, INTEG>;
+    auto k = fused_small_kernel<Real, D, INTEG, EXPM>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, warps * 32, smem, st>>>(p);
     return cudaGetLastError();
 }
 
-template <typename Real, int D, int INTEG>
+template <typename Real, int D, int INTEG, int EXPM = 0>
 int fused_max_blocks_per_sm(int warps, size_t smem) {
     int nb = 0;
-    auto k = fused_small_kernel<Real, D, INTEG>;
+    auto k = fused_small_kernel<Real, D, INTEG, EXPM>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, warps * 32, smem) != cudaSuccess) return 0;
     return nb;

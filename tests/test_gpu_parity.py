@@ -329,3 +329,54 @@ def test_coupled_spins_slice_of_run(prop):
     assert np.max(np.abs(U - R)) <= TOL64
     U32 = run(prop, full, "fp32", h_dtype=None)
     assert np.max(np.abs(U32 - ref32(full))) <= tol32(16, full.n_steps)
+
+
+# --- the paper's Chebyshev exponential (Sec. 2.1, Algorithm 1) ------------------------------------
+
+
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+@pytest.mark.parametrize("d", [2, 3, 8, 16])
+def test_chebyshev_fp64_matches_oracle(prop, integrator, d):
+    from paper_2108_07126_gb300 import binding as b
+
+    prob = wl.random_problem(d, 2, 333, integrator, seed=1000 + d, g_norm=0.5)
+    prop.set_option(b.PARAMENT_OPT_EXP_METHOD, 1)
+    U = run(prop, prob, "fp64")
+    assert np.max(np.abs(U - ref(prob))) <= TOL64
+    st = prop.stats()
+    # one product per degree and slice: exp_products = m N with m the global degree
+    assert st["exp_products"] == st["max_degree"] * prob.n_steps and st["max_squarings"] == 0
+
+
+@pytest.mark.parametrize("d", [4, 16])
+def test_chebyshev_fp32_matches_oracle(prop, d):
+    from paper_2108_07126_gb300 import binding as b
+
+    prob = wl.random_problem(d, 3, 1000, "magnus4_gl2", seed=1100 + d, g_norm=0.4)
+    prop.set_option(b.PARAMENT_OPT_EXP_METHOD, 1)
+    U = run(prop, prob, "fp32")
+    assert np.max(np.abs(U - ref32(prob))) <= tol32(d, prob.n_steps)
+
+
+def test_chebyshev_degree_follows_the_bound(prop):
+    """A larger spectral interval needs a higher Chebyshev degree (Table 1 grows with m)."""
+    from paper_2108_07126_gb300 import binding as b
+
+    degs = []
+    for g in (0.05, 0.5, 3.0):
+        prob = wl.random_problem(4, 1, 20, "midpoint", seed=1200, g_norm=g)
+        prop.set_option(b.PARAMENT_OPT_EXP_METHOD, 1)
+        U = run(prop, prob, "fp64")
+        assert np.max(np.abs(U - ref(prob))) <= TOL64 * max(1.0, g)
+        degs.append(prop.stats()["max_degree"])
+    assert degs[0] < degs[1] < degs[2]
+
+
+def test_chebyshev_needs_small_d(prop):
+    from paper_2108_07126_gb300 import binding as b
+
+    prob = wl.random_problem(32, 1, 5, "midpoint", seed=1)
+    prop.set_option(b.PARAMENT_OPT_EXP_METHOD, 1)
+    with pytest.raises(b.ParamentError) as e:
+        run(prop, prob, "fp64")
+    assert e.value.status == b.PARAMENT_ERR_UNSUPPORTED
