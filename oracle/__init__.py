@@ -18,4 +18,6 @@ from .parament_oracle import (  # noqa: F401
     propagate,
     samples_per_run,
     slice_exponents,
+    trajectory,
+    trajectory_times,
 )

@@ -29,6 +29,11 @@ What it computes, each piece following the paper's definitions:
   on the left) evaluated by the pairwise tree of Sec. 2.2: consecutive pairs
   are multiplied, the number of matrices halves each round, an odd leftover
   (the latest slice) is carried to the next round unchanged.
+* ``trajectory``         -- the propagator at intermediate times, U(t_n) = U_n ... U_1
+  for n = every, 2 every, ... and the last slice N (Sec. 2, Eq. slices read at
+  t_n instead of T), or the states psi(t_n) = U(t_n) psi_0 (Sec. 2, the state
+  form of the Schroedinger equation); a plain sequential left-multiplication
+  in time order.
 * ``loss_and_gradient``  -- gate-fidelity loss L = 1 - |Tr(V^dagger U)|^2 / d^2 and
   dL/dc_k(t_j) for the midpoint rule, with the Frechet derivative of exp taken
   from the Daleckii-Krein formula (Sec. 7 motivates the gradient for GRAPE;
@@ -148,6 +153,37 @@ def propagate(H0, Hk, c, dt: float, integrator: str = MIDPOINT) -> np.ndarray:
     """Full propagator U(T) = U_N ... U_1 (Sec. 2, Eq. slices)."""
     G = slice_exponents(H0, Hk, c, dt, integrator)
     return ordered_product(exact_slice_propagators(G))
+
+
+def trajectory_times(n_steps: int, every: int) -> np.ndarray:
+    """Slice counts n of the outputs: every, 2 every, ..., and n_steps if it is not a multiple."""
+    n = np.arange(every, n_steps + 1, every, dtype=np.int64)
+    if n_steps % every:
+        n = np.append(n, n_steps)
+    return n
+
+
+def trajectory(H0, Hk, c, dt: float, integrator: str = MIDPOINT, every: int = 1, psi0=None) -> np.ndarray:
+    """U(t_n) = U_n ... U_1 at n in ``trajectory_times(N, every)`` (Sec. 2, Eq. slices).
+
+    Sequential: R <- U_j R for j = 1..N (later slice on the left), R kept at the
+    output slices.  With ``psi0`` (length d) the states psi(t_n) = U(t_n) psi0
+    are returned instead, shape (n_out, d); otherwise (n_out, d, d).
+    """
+    G = slice_exponents(H0, Hk, c, dt, integrator)
+    Us = exact_slice_propagators(G)
+    N, d = G.shape[0], np.asarray(H0).shape[-1]
+    keep = set(int(n) for n in trajectory_times(N, every))
+    R = np.eye(d, dtype=np.complex128)
+    out = []
+    for j in range(N):
+        R = Us[j] @ R
+        if j + 1 in keep:
+            out.append(R.copy())
+    out = np.array(out, dtype=np.complex128).reshape(len(out), d, d)
+    if psi0 is not None:
+        return out @ np.asarray(psi0, dtype=np.complex128)
+    return out
 
 
 def gate_loss(U: np.ndarray, V: np.ndarray) -> float:

@@ -134,6 +134,93 @@ def test_rabi_workload_rwa_population():
     assert abs(U[1, 0]) ** 2 > 0.99
 
 
+# --- trajectories: the propagator at every intermediate time -------------------------------
+
+
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+def test_trajectory_static_hamiltonian_is_exact_at_every_time(integrator):
+    # all c constant: U(t_n) = exp(-i H n dt) at every output time, for any stride
+    rng = np.random.default_rng(11)
+    d, K, N, dt = 4, 2, 13, 0.21
+    H0 = wl.random_hermitian(rng, d)
+    Hk = np.stack([wl.random_hermitian(rng, d) for _ in range(K)])
+    amp = rng.standard_normal(K)
+    c = np.repeat(amp[:, None], wl.n_samples(N, integrator), axis=1)
+    H = H0 + np.einsum("k,kab->ab", amp, Hk)
+    for every in (1, 4, 13, 20):
+        times = oracle.trajectory_times(N, every)
+        traj = oracle.trajectory(H0, Hk, c, dt, integrator, every)
+        assert traj.shape == (len(times), d, d)
+        for n, U in zip(times, traj):
+            assert np.max(np.abs(U - scipy.linalg.expm(-1j * H * (n * dt)))) < 1e-12
+
+
+def test_trajectory_times_cover_the_last_slice():
+    assert list(oracle.trajectory_times(10, 3)) == [3, 6, 9, 10]
+    assert list(oracle.trajectory_times(9, 3)) == [3, 6, 9]
+    assert list(oracle.trajectory_times(5, 1)) == [1, 2, 3, 4, 5]
+    assert list(oracle.trajectory_times(4, 7)) == [4]
+    assert len(oracle.trajectory_times(0, 2)) == 0
+
+
+@pytest.mark.parametrize("integrator", ["magnus4_gl2", "magnus4_simpson"])
+def test_trajectory_follows_circular_drive_closed_form(integrator):
+    # every intermediate U(t_n) against the closed form of the circular drive (Sec. 5)
+    p = _circular_params()
+    N, every = 2048, 64
+    prob = wl.circular_drive(N, integrator, p["w0"], p["w1"], p["w_rf"], p["t_final"])
+    traj = oracle.trajectory(prob.H0, prob.Hk, prob.c, prob.dt, integrator, every)
+    for n, U in zip(oracle.trajectory_times(N, every), traj):
+        ref = circular_exact(p["w0"], p["w1"], p["w_rf"], n * prob.dt)
+        assert np.max(np.abs(U - ref)) < 1e-10
+
+
+def test_trajectory_resonant_rabi_population_over_time():
+    # w0 = w_rf: P_1(t) = sin^2(w1 t / 2) at every output time; states from psi0 = |0>
+    w1, t = 0.1, 40.0
+    N, every = 4000, 100
+    prob = wl.circular_drive(N, "magnus4_gl2", 1.0, w1, 1.0, t)
+    psi = oracle.trajectory(prob.H0, prob.Hk, prob.c, prob.dt, prob.integrator, every, psi0=np.array([1.0, 0.0]))
+    times = oracle.trajectory_times(N, every) * prob.dt
+    P1 = np.abs(psi[:, 1]) ** 2
+    assert np.max(np.abs(P1 - np.sin(0.5 * w1 * times) ** 2)) < 1e-10
+    assert P1.max() > 0.99  # a full Rabi flop happens inside the window
+
+
+def test_trajectory_last_entry_is_the_tree_product():
+    # sequential prefix products end at the pairwise-tree U(T) (two orders of evaluation)
+    prob = wl.random_problem(5, 3, 37, "magnus4_gl2", seed=12, g_norm=0.8)
+    traj = oracle.trajectory(prob.H0, prob.Hk, prob.c, prob.dt, prob.integrator, 5)
+    U = oracle.propagate(prob.H0, prob.Hk, prob.c, prob.dt, prob.integrator)
+    assert np.max(np.abs(traj[-1] - U)) < 1e-13
+    psi0 = wl.haar_unitary(np.random.default_rng(13), 5)[:, 0]
+    psi = oracle.trajectory(prob.H0, prob.Hk, prob.c, prob.dt, prob.integrator, 5, psi0=psi0)
+    assert np.max(np.abs(psi - traj @ psi0)) < 1e-14
+
+
+def _circular_trajectory_error(fn_traj, every=256, N=1024):
+    p = _circular_params()
+    prob = wl.circular_drive(N, "magnus4_gl2", p["w0"], p["w1"], p["w_rf"], p["t_final"])
+    traj = fn_traj(prob.H0, prob.Hk, prob.c, prob.dt, prob.integrator, every)
+    return max(np.max(np.abs(U - circular_exact(p["w0"], p["w1"], p["w_rf"], n * prob.dt)))
+               for n, U in zip(oracle.trajectory_times(N, every), traj))
+
+
+def test_planted_transposed_slices_fail_trajectory_closed_form(monkeypatch):
+    # a row/column-major mix-up of the slice propagators (U_j^T) breaks the intermediate closed forms
+    assert _circular_trajectory_error(orc.trajectory) < 1e-8
+    real = orc.exact_slice_propagators
+    monkeypatch.setattr(orc, "exact_slice_propagators", lambda G: np.swapaxes(real(G), -1, -2))
+    assert _circular_trajectory_error(orc.trajectory) > 1e-3
+
+
+def test_planted_off_by_one_output_time_fails_closed_form(monkeypatch):
+    # keeping R one slice early (after slice n - 1 instead of n) is caught at the step size
+    real = orc.trajectory_times
+    monkeypatch.setattr(orc, "trajectory_times", lambda n, every: real(n, every) - 1)
+    assert _circular_trajectory_error(orc.trajectory) > 1e-4
+
+
 # --- brute-force ODE integration ---------------------------------------------------------
 
 
