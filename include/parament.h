@@ -226,6 +226,24 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec);
 int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, void *grad_out, void *U_out,
                             parament_precision prec);
 
+/*
+ * Trajectory: the propagator (or a state) at intermediate times (Sec. 2: Eq. slices read at
+ * t_n = n dt instead of T; the states psi(t) = U(t) psi_0 of the Schroedinger equation).
+ * Outputs after slices n = every, 2 every, ..., and after the last slice N when N is not a
+ * multiple of `every`: n_out = ceil(N / every) entries, output o after min((o + 1) every, N) slices.
+ *   psi0 == NULL: out = U(t_n), [n_out][d][d] complex (the dtype of set_hamiltonians)
+ *   psi0 != NULL: out = U(t_n) psi0, [n_out][d] complex; psi0 is [d] in the same dtype
+ * Pointers host or device (a host `out` is filled before the call returns).  The library writes
+ * out and keeps no reference to it or to psi0 after the call.  Method: one forward pass that keeps
+ * every leaf and block product, exclusive FP64 prefix scans over them (as for the gradient), then a
+ * second pass in which every leaf starts from its prefix and writes its running product at the
+ * output slices.  Taylor exponential, FP64 or FP32, d <= 16, every integrator.  N = 0 writes
+ * nothing (out may then be NULL).  Errors: INVALID_VALUE for a null out or every < 1; UNSUPPORTED for d > 16, tensor-core
+ * precisions or the Chebyshev option; STATE before set_controls.
+ */
+int parament_propagate_trajectory(parament_ctx *ctx, const void *psi0, void *out, int64_t every,
+                                  parament_precision prec);
+
 /* One problem of a batched call; all pointers are device memory owned by the caller. */
 typedef struct {
     int dim;            /* d, 1..128 */

@@ -118,6 +118,7 @@ _SIGS = {
     "parament_set_controls": ([_vp, _vp, ctypes.c_int, ctypes.c_int64, ctypes.c_double], ctypes.c_int),
     "parament_propagate": ([_vp, _vp, ctypes.c_int], ctypes.c_int),
     "parament_propagate_grad": ([_vp, _vp, ctypes.POINTER(ctypes.c_double), _vp, _vp, ctypes.c_int], ctypes.c_int),
+    "parament_propagate_trajectory": ([_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int], ctypes.c_int),
     "parament_get_stats": ([_vp, ctypes.POINTER(parament_stats)], ctypes.c_int),
     "parament_set_option": ([_vp, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
     "parament_get_option": ([_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
@@ -203,6 +204,10 @@ def parament_propagate_grad(ctx, V_ptr: int, grad_ptr: int, U_ptr: int | None, p
     _check(_lib.parament_propagate_grad(ctx, V_ptr, ctypes.byref(loss) if want_loss else None, grad_ptr,
                                         U_ptr or None, int(prec)), ctx)
     return loss.value if want_loss else None
+
+
+def parament_propagate_trajectory(ctx, psi0_ptr: int | None, out_ptr: int | None, every: int, prec: int) -> None:
+    _check(_lib.parament_propagate_trajectory(ctx, psi0_ptr or None, out_ptr or None, int(every), int(prec)), ctx)
 
 
 def parament_get_stats(ctx) -> dict:
@@ -359,6 +364,21 @@ class Propagator:
             out = torch.empty(self.dim, self.dim, dtype=self.dtype, device=self.device)
         self._sync_stream()
         parament_propagate(self.ctx, out.data_ptr(), PRECISIONS[prec])
+        return out
+
+    def propagate_trajectory(self, prec: str = "fp64", every: int = 1, psi0=None, out=None):
+        """U(t_n) (n_out, d, d), or psi(t_n) = U(t_n) psi0 (n_out, d), after slices every, 2 every, ..., N."""
+        torch = self._torch
+        n_out = -(-self.n_steps // every) if every > 0 else 0
+        psi = None
+        if psi0 is not None:
+            psi = torch.as_tensor(psi0).to(self.dtype).to(self.device).contiguous()
+        if out is None:
+            shape = (n_out, self.dim) if psi is not None else (n_out, self.dim, self.dim)
+            out = torch.empty(shape, dtype=self.dtype, device=self.device)
+        self._sync_stream()
+        parament_propagate_trajectory(self.ctx, psi.data_ptr() if psi is not None else None,
+                                      out.data_ptr() if out.numel() else None, every, PRECISIONS[prec])
         return out
 
     def propagate_grad(self, V, prec: str = "fp64", want_U: bool = False):

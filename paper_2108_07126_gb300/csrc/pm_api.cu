@@ -27,6 +27,7 @@ namespace pm {
     size_t fused_smem_d##D(int, int, int);                                                               \
     int fused_groups_per_warp_d##D(int);                                                                 \
     cudaError_t grad_run_d##D(int, const ScanParams &, const GradParams &, int, int, size_t, cudaStream_t); \
+    cudaError_t scan_run_d##D(const ScanParams &, cudaStream_t);                                          \
     int adjoint_blocks_per_sm_d##D(int, int, size_t);                                                     \
     size_t adjoint_smem_d##D(int, int, int);
 PM_DECL_D(2)
@@ -87,6 +88,8 @@ struct parament_ctx {
     Workspace hraw, full, packed64, packed32, bnorm, partials, tickets, counters, status, check;
     Workspace ctrl_copy, ctrl_conv, uout, bmax, cpacked64, cpacked32, cbnorm;
     Workspace gv, gvdag, gleaf, gblock, gbpin, gpin, gz, gpbuf, gckpt, ggrad, lscratch;
+    Workspace tstage, tpsi;  // trajectory: staging of a host output, psi_0 padded (FP64)
+    std::vector<double2> tpsi_host;
     // batched plan
     Workspace bparams, binsts, btable, bitems, bfull, bpacked, bnorms, bpartials, btickets, bcounters, bstatus,
         bqueue, bscratch;
@@ -550,6 +553,15 @@ cudaError_t grad_run(int Dp, int fp64, const ScanParams &sp, const GradParams &g
     }
     return cudaErrorInvalidValue;
 }
+cudaError_t scan_run(int Dp, const ScanParams &sp, cudaStream_t st) {
+    switch (Dp) {
+        case 2: return scan_run_d2(sp, st);
+        case 4: return scan_run_d4(sp, st);
+        case 8: return scan_run_d8(sp, st);
+        case 16: return scan_run_d16(sp, st);
+    }
+    return cudaErrorInvalidValue;
+}
 int adjoint_blocks_per_sm(int Dp, int fp64, int warps, size_t smem) {
     switch (Dp) {
         case 2: return adjoint_blocks_per_sm_d2(fp64, warps, smem);
@@ -735,7 +747,7 @@ int parament_destroy(parament_ctx *ctx) {
                             &ctx->gbpin, &ctx->gpin, &ctx->gz, &ctx->gpbuf, &ctx->gckpt, &ctx->ggrad, &ctx->lscratch,
                             &ctx->bparams, &ctx->binsts, &ctx->btable, &ctx->bitems, &ctx->bfull, &ctx->bpacked,
                             &ctx->bnorms, &ctx->bpartials, &ctx->btickets, &ctx->bcounters, &ctx->bstatus,
-                            &ctx->bqueue, &ctx->bscratch, &ctx->cheb};
+                            &ctx->bqueue, &ctx->bscratch, &ctx->cheb, &ctx->tstage, &ctx->tpsi};
         if (ctx->b_exec) cudaGraphExecDestroy(ctx->b_exec);
         for (Workspace *w : all) ws_free(*w);
     }
@@ -1007,6 +1019,13 @@ __global__ void vdag_kernel(const InT *V, int d, int Dp, double2 *out) {
     }
 }
 
+// psi_0 padded with zeros to Dp entries, in FP64
+template <typename InT>
+__global__ void psi_pad_kernel(const InT *psi, int d, int Dp, double2 *out) {
+    for (int t = threadIdx.x; t < Dp; t += blockDim.x)
+        out[t] = t < d ? make_double2((double)psi[t].x, (double)psi[t].y) : make_double2(0.0, 0.0);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1232,6 +1251,107 @@ int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, 
         PM_CUDA(cudaStreamSynchronize(ctx->stream));
         *loss_out = z[2];
     } else if (host_g || host_u) {
+        PM_CUDA(cudaStreamSynchronize(ctx->stream));
+    }
+    return PARAMENT_OK;
+}
+
+int parament_propagate_trajectory(parament_ctx *ctx, const void *psi0, void *out, int64_t every,
+                                  parament_precision prec) {
+    if (!ctx) return PARAMENT_ERR_INVALID_VALUE;
+    ctx->err.clear();
+    if (ctx->state < 2) return set_err(ctx, PARAMENT_ERR_STATE, "set_hamiltonians and set_controls must come first");
+    if (every < 1) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "every must be >= 1");
+    if (!out && ctx->n_steps > 0) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "null out");
+    if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "trajectory precision must be FP64 or FP32");
+    if (ctx->dpad > kMaxSmallDim)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "trajectories cover d <= %d", kMaxSmallDim);
+    if (ctx->opt_exp_method != 0)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "trajectories use the Taylor exponential");
+    DeviceGuard guard(ctx->device);
+    const int fp64 = prec == PARAMENT_PREC_FP64;
+    const int Dp = ctx->dpad, d = ctx->dim;
+    const size_t DD = (size_t)Dp * Dp;
+    const size_t esz = ctx->dtype == PARAMENT_C128 ? 16 : 8;
+    const int64_t N = ctx->n_steps;
+    const int64_t n_out = (N + every - 1) / every;
+    const size_t obytes = (size_t)n_out * (psi0 ? (size_t)d : (size_t)d * d) * esz;
+    if (n_out == 0) return PARAMENT_OK;
+    int st;
+
+    // psi_0 (host or device) -> padded FP64
+    const double2 *psi_dev = nullptr;
+    if (psi0) {
+        if ((st = ws_reserve(ctx, ctx->tpsi, (size_t)Dp * sizeof(double2)))) return st;
+        if (is_device_ptr(psi0)) {
+            if (ctx->dtype == PARAMENT_C128)
+                psi_pad_kernel<double2><<<1, 32, 0, ctx->stream>>>((const double2 *)psi0, d, Dp, (double2 *)ctx->tpsi.ptr);
+            else
+                psi_pad_kernel<float2><<<1, 32, 0, ctx->stream>>>((const float2 *)psi0, d, Dp, (double2 *)ctx->tpsi.ptr);
+            PM_CUDA(cudaGetLastError());
+        } else {
+            ctx->tpsi_host.assign(Dp, make_double2(0.0, 0.0));
+            for (int i = 0; i < d; ++i) {
+                if (ctx->dtype == PARAMENT_C128) ctx->tpsi_host[i] = ((const double2 *)psi0)[i];
+                else ctx->tpsi_host[i] = make_double2(((const float2 *)psi0)[i].x, ((const float2 *)psi0)[i].y);
+            }
+            PM_CUDA(cudaMemcpyAsync(ctx->tpsi.ptr, ctx->tpsi_host.data(), (size_t)Dp * sizeof(double2),
+                                    cudaMemcpyHostToDevice, ctx->stream));
+        }
+        psi_dev = (const double2 *)ctx->tpsi.ptr;
+    }
+    const bool host_out = !is_device_ptr(out);
+    void *odst = out;
+    if (host_out) {
+        if ((st = ws_reserve(ctx, ctx->tstage, obytes))) return st;
+        odst = ctx->tstage.ptr;
+    } else if ((uintptr_t)out % esz) {
+        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "out not aligned to its element size");
+    }
+
+    // forward pass keeping every leaf and block product (U(T) into the scratch output)
+    if ((st = ws_reserve(ctx, ctx->uout, (size_t)d * d * esz))) return st;
+    FusedParams p;
+    int grid = 0, warps = 0, lpb = 0;
+    size_t smem = 0;
+    if ((st = forward_setup(ctx, fp64, ctx->uout.ptr, p, grid, warps, smem, lpb))) return st;
+    const int64_t L = (int64_t)grid * lpb;
+    if ((st = ws_reserve(ctx, ctx->gleaf, (size_t)L * DD * sizeof(double2)))) return st;
+    if ((st = ws_reserve(ctx, ctx->gblock, (size_t)grid * DD * sizeof(double2)))) return st;
+    if ((st = ws_reserve(ctx, ctx->gbpin, 2 * (size_t)grid * DD * sizeof(double2)))) return st;
+    if ((st = ws_reserve(ctx, ctx->gpin, 2 * (size_t)L * DD * sizeof(double2)))) return st;
+    p.leaf_out = (double2 *)ctx->gleaf.ptr;
+    p.block_out = (double2 *)ctx->gblock.ptr;
+    PM_CUDA(fused_dispatch(Dp, fp64, (int)ctx->integ, p, grid, warps, smem, ctx->stream));
+    record_launch(ctx, ctx->nb_eff, grid, warps, lpb);
+
+    // exclusive prefix of every leaf (FP64)
+    ScanParams sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.leafpart = (const double2 *)ctx->gleaf.ptr;
+    sp.blockpart = (const double2 *)ctx->gblock.ptr;
+    sp.n_blocks = grid;
+    sp.leaves_per_block = lpb;
+    sp.bpin = (double2 *)ctx->gbpin.ptr;
+    sp.bsout = sp.bpin + (size_t)grid * DD;
+    sp.pin = (double2 *)ctx->gpin.ptr;
+    sp.sout = sp.pin + (size_t)L * DD;
+    sp.d_out = d;
+    PM_CUDA(scan_run(Dp, sp, ctx->stream));
+
+    // second pass: every leaf from its prefix, running product at the output slices
+    FusedParams pt = p;
+    pt.leaf_out = nullptr;
+    pt.block_out = nullptr;
+    pt.traj_pin = sp.pin;
+    pt.traj_out = odst;
+    pt.traj_psi0 = psi_dev;
+    pt.traj_every = every;
+    PM_CUDA(fused_dispatch(Dp, fp64, (int)ctx->integ, pt, grid, warps, smem, ctx->stream, 2));
+
+    if (host_out) {
+        PM_CUDA(cudaMemcpyAsync(out, odst, obytes, cudaMemcpyDeviceToHost, ctx->stream));
         PM_CUDA(cudaStreamSynchronize(ctx->stream));
     }
     return PARAMENT_OK;

@@ -74,6 +74,10 @@ struct FusedParams {
     const int *cheb_m;         // Chebyshev mode: degree, 1 / beta and coefficients (device, written by
     const double *cheb_inv_beta;  //   cheb_coef_kernel)
     const void *cheb_coef;     // Real complex [m + 1]: a_k = (-i)^k J_k(beta)
+    const double2 *traj_pin;   // trajectory mode: exclusive prefix of every leaf, FP64 [n_leaves][D][D]
+    void *traj_out;            // trajectory mode: U(t_n) [n_out][d][d] or psi(t_n) [n_out][d] (U_out's dtype)
+    const double2 *traj_psi0;  // trajectory mode: psi_0 padded to D in FP64, or null for U(t_n)
+    int64_t traj_every;        // trajectory mode: outputs after slices every, 2 every, ..., and the last
     int n_cls;
     double cls_cap[kMaxClasses];
     int cls_code[kMaxClasses];

@@ -260,6 +260,9 @@ template <> __device__ __forceinline__ void ld4<double>(const double *p, double 
 // The whole propagation of one problem, executed by thread block `blk` of the
 // `nblk` blocks assigned to it (the grid of fused_small_kernel, or the blocks
 // of one instance of the batched kernel).  smem: the dynamic shared memory.
+// EXPM: 0 = Taylor exponential, 1 = Chebyshev exponential, 2 = Taylor in
+// trajectory mode (every leaf starts from its exclusive prefix p.traj_pin and
+// writes U(t_n) or psi(t_n) at the output slices; no tree, no statistics).
 template <typename Real, int D, int INTEG, int EXPM = 0>
 __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nblk, unsigned char *smem) {
     using G = Geo<Real, D>;
@@ -300,17 +303,59 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
     const int len = active_warp ? (int)(p.n_steps * (leaf + 1) / n_leaves - j0) : 0;
     const int wlen = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
 
-    // R = I
+    // R = I (trajectory mode: R = the product of all slices before the leaf)
     if (active_warp) {
         C t[TR][TC];
 #pragma unroll
         for (int r = 0; r < TR; ++r)
 #pragma unroll
-            for (int c = 0; c < TC; ++c)
-                t[r][c] = Cx<Real>::make((rb + r * G::RBN) == G::col(cb, c) ? Real(1) : Real(0), Real(0));
+            for (int c = 0; c < TC; ++c) {
+                const int i = rb + r * G::RBN, jj = G::col(cb, c);
+                if constexpr (EXPM == 2) {
+                    const double2 v = p.traj_pin[(size_t)leaf * DD + i * D + jj];
+                    t[r][c] = Cx<Real>::make((Real)v.x, (Real)v.y);
+                } else {
+                    t[r][c] = Cx<Real>::make(i == jj ? Real(1) : Real(0), Real(0));
+                }
+            }
         st_tile<Real, D>(SR, rb, cb, t);
     }
     __syncthreads();
+
+    // trajectory mode: after slice j, R = U(t_{j+1}); keep it at the output slices
+    auto traj_emit = [&](int64_t j, const C (&R)[TR][TC]) {
+        const int64_t n1 = j + 1;
+        if (n1 % p.traj_every != 0 && n1 != p.n_steps) return;
+        const int64_t o = j / p.traj_every;
+        const int d = p.d_out;
+        if (p.traj_psi0 == nullptr) {
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int c = 0; c < TC; ++c) {
+                    const int i = rb + r * G::RBN, jj = G::col(cb, c);
+                    if (i < d && jj < d) {
+                        const size_t at = ((size_t)o * d + i) * d + jj;
+                        if (p.out_c128) ((double2 *)p.traj_out)[at] = make_double2((double)R[r][c].x, (double)R[r][c].y);
+                        else ((float2 *)p.traj_out)[at] = make_float2((float)R[r][c].x, (float)R[r][c].y);
+                    }
+                }
+        } else {  // psi(t_n) = R psi_0, rows gl, gl + LANES, ... (R is in SR)
+            for (int i = gl; i < d; i += LANES) {
+                Real re = 0, im = 0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    const C a = SR[i * LD + k];
+                    const double2 b = p.traj_psi0[k];
+                    re = fma(a.x, (Real)b.x, fma(-a.y, (Real)b.y, re));
+                    im = fma(a.x, (Real)b.y, fma(a.y, (Real)b.x, im));
+                }
+                const size_t at = (size_t)o * d + i;
+                if (p.out_c128) ((double2 *)p.traj_out)[at] = make_double2((double)re, (double)im);
+                else ((float2 *)p.traj_out)[at] = make_float2((float)re, (float)im);
+            }
+        }
+    };
 
     unsigned flags = 0;
     unsigned long long n_exp = 0, n_tree = 0;
@@ -322,7 +367,7 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
             const bool act = (t0 + gl) < len;
             Real *gcol = gam + lane;
             slice_coefficients<Real, INTEG>(p, j0 + t0 + gl, act, gcol);
-            if (EXPM == 0) {
+            if (EXPM != 1) {
                 double nu = 0.0;
                 for (int e = 0; e < nb; ++e) nu = fma(fabs((double)gcol[e * 32]), bnorm[e], nu);
                 cls[lane] = find_class(p, nu, &flags);
@@ -545,6 +590,9 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
                 } else {
                     st_tile<Real, D>(SR, rb, cb, acc);
                     __syncwarp();
+                    if constexpr (EXPM == 2) {
+                        if ((t0 + rr) < len) traj_emit(j0 + t0 + rr, acc);
+                    }
                 }
             }
 
@@ -557,6 +605,9 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
         }
         __syncwarp();
     }
+
+    // trajectory mode: the forward pass already combined the leaves and recorded statistics
+    if constexpr (EXPM == 2) return;
 
     // ---- optional: every leaf product in FP64 (checkpoints of the adjoint pass)
     if (p.leaf_out && active_warp) {

@@ -1,12 +1,12 @@
 // Instantiations of the fused propagation kernel for padded dimension 2
-// (Taylor exponential; Chebyshev exponential when cheb != 0).
+// (mode cheb: 0 = Taylor exponential, 1 = Chebyshev exponential, 2 = Taylor trajectory).
 #include "pm_fused.cuh"
 
 namespace pm {
 
 cudaError_t fused_dispatch_d2(int fp64, int integ, const FusedParams &p, int grid, int warps, size_t smem,
                                cudaStream_t st, int cheb) {
-    switch ((cheb ? 6 : 0) + integ * 2 + (fp64 ? 1 : 0)) {
+    switch (cheb * 6 + integ * 2 + (fp64 ? 1 : 0)) {
         case 0: return launch_fused<float, 2, kMidpoint>(p, grid, warps, smem, st);
         case 1: return launch_fused<double, 2, kMidpoint>(p, grid, warps, smem, st);
         case 2: return launch_fused<float, 2, kGL2>(p, grid, warps, smem, st);
@@ -19,12 +19,18 @@ cudaError_t fused_dispatch_d2(int fp64, int integ, const FusedParams &p, int gri
         case 9: return launch_fused<double, 2, kGL2, 1>(p, grid, warps, smem, st);
         case 10: return launch_fused<float, 2, kSimpson, 1>(p, grid, warps, smem, st);
         case 11: return launch_fused<double, 2, kSimpson, 1>(p, grid, warps, smem, st);
+        case 12: return launch_fused<float, 2, kMidpoint, 2>(p, grid, warps, smem, st);
+        case 13: return launch_fused<double, 2, kMidpoint, 2>(p, grid, warps, smem, st);
+        case 14: return launch_fused<float, 2, kGL2, 2>(p, grid, warps, smem, st);
+        case 15: return launch_fused<double, 2, kGL2, 2>(p, grid, warps, smem, st);
+        case 16: return launch_fused<float, 2, kSimpson, 2>(p, grid, warps, smem, st);
+        case 17: return launch_fused<double, 2, kSimpson, 2>(p, grid, warps, smem, st);
     }
     return cudaErrorInvalidValue;
 }
 
 int fused_blocks_per_sm_d2(int fp64, int integ, int warps, size_t smem, int cheb) {
-    switch ((cheb ? 6 : 0) + integ * 2 + (fp64 ? 1 : 0)) {
+    switch (cheb * 6 + integ * 2 + (fp64 ? 1 : 0)) {
         case 0: return fused_max_blocks_per_sm<float, 2, kMidpoint>(warps, smem);
         case 1: return fused_max_blocks_per_sm<double, 2, kMidpoint>(warps, smem);
         case 2: return fused_max_blocks_per_sm<float, 2, kGL2>(warps, smem);
@@ -37,6 +43,12 @@ int fused_blocks_per_sm_d2(int fp64, int integ, int warps, size_t smem, int cheb
         case 9: return fused_max_blocks_per_sm<double, 2, kGL2, 1>(warps, smem);
         case 10: return fused_max_blocks_per_sm<float, 2, kSimpson, 1>(warps, smem);
         case 11: return fused_max_blocks_per_sm<double, 2, kSimpson, 1>(warps, smem);
+        case 12: return fused_max_blocks_per_sm<float, 2, kMidpoint, 2>(warps, smem);
+        case 13: return fused_max_blocks_per_sm<double, 2, kMidpoint, 2>(warps, smem);
+        case 14: return fused_max_blocks_per_sm<float, 2, kGL2, 2>(warps, smem);
+        case 15: return fused_max_blocks_per_sm<double, 2, kGL2, 2>(warps, smem);
+        case 16: return fused_max_blocks_per_sm<float, 2, kSimpson, 2>(warps, smem);
+        case 17: return fused_max_blocks_per_sm<double, 2, kSimpson, 2>(warps, smem);
     }
     return 0;
 }

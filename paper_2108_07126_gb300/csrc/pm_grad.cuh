@@ -64,7 +64,7 @@ struct ScanParams {
     int n_blocks, leaves_per_block;
     double2 *bpin, *bsout;    // [n_blocks][D][D]
     double2 *pin, *sout;      // [L][D][D]
-    const double2 *vdag;      // [D][D]
+    const double2 *vdag;      // [D][D], or null (no z, no loss)
     double *z;                // [3]: Re z, Im z, loss
     void *U_out;              // optional d x d
     int out_c128, d_out;
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256) scan_blocks_kernel(const ScanParams sp) {
         U[e] = v;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && sp.vdag) {
         double2 z = make_double2(0.0, 0.0);
         for (int i = 0; i < D; ++i)
             for (int k = 0; k < D; ++k) cfma(z, sp.vdag[i * D + k], U[k * D + i]);

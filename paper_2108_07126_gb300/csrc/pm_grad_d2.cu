@@ -24,6 +24,15 @@ cudaError_t grad_run_d2(int fp64, const ScanParams &sp, const GradParams &gp, in
     return cudaGetLastError();
 }
 
+// exclusive prefixes and suffixes of every leaf from the forward pass's leaf and block products
+cudaError_t scan_run_d2(const ScanParams &sp, cudaStream_t st) {
+    scan_blocks_kernel<2><<<1, 256, 0, st>>>(sp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    scan_leaves_kernel<2><<<sp.n_blocks, 256, 0, st>>>(sp);
+    return cudaGetLastError();
+}
+
 int adjoint_blocks_per_sm_d2(int fp64, int warps, size_t smem) {
     int nb = 0;
     cudaError_t e;

@@ -4,7 +4,9 @@
 
 Workloads: ``rabi`` (d = 2, midpoint), ``spins`` (d = 16, GL4 Magnus), ``gradient``
 (d = 8, loss + adjoint gradient), ``dense`` (d = 128, GL4 Magnus), ``batched``
-(mixed instances, d up to 64, one persistent launch).  Times are CUDA events on the
+(mixed instances, d up to 64, one persistent launch).  ``--exp chebyshev`` selects the
+paper's Chebyshev exponential, ``--traj-every n`` times the trajectory U(t_n) instead of
+U(T).  Times are CUDA events on the
 launching stream around each call, after one warm-up call.
 """
 
@@ -42,6 +44,9 @@ def main(argv=None):
     ap.add_argument("--n-steps", type=int, default=0, help="slices (0 = the workload's default)")
     ap.add_argument("--n-inst", type=int, default=256, help="instances of the batched workload")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--exp", choices=["taylor", "chebyshev"], default="taylor", help="exponential of propagate")
+    ap.add_argument("--traj-every", type=int, default=0,
+                    help="time the trajectory U(t_n) every this many slices instead of U(T)")
     args = ap.parse_args(argv)
     prec = args.prec
     cdt = torch.complex128 if prec == "fp64" else torch.complex64
@@ -57,12 +62,19 @@ def main(argv=None):
         make = {"rabi": wl.rabi_qubit, "spins": wl.coupled_spins, "gradient": wl.gradient_qubits,
                 "dense": wl.dense_stress}[args.workload]
         prob = make(n_steps=args.n_steps) if args.n_steps else make()
+        if args.exp == "chebyshev":
+            prop.set_option(b.PARAMENT_OPT_EXP_METHOD, 1)
         prop.set_hamiltonians(torch.as_tensor(prob.H0).to(cdt), torch.as_tensor(prob.Hk).to(cdt), prob.integrator)
         prop.set_controls(torch.as_tensor(prob.c).to(rdt).cuda(), prob.dt, prob.n_steps)
         res["n_steps"] = prob.n_steps
         if args.workload == "gradient":
             V = torch.as_tensor(prob.V).to(cdt).cuda()
             ms = _time(lambda: prop.propagate_grad(V, prec), args.reps)
+        elif args.traj_every > 0:
+            n_out = -(-prob.n_steps // args.traj_every)
+            T = torch.empty(n_out, prob.dim, prob.dim, dtype=cdt, device="cuda")
+            ms = _time(lambda: prop.propagate_trajectory(prec, args.traj_every, out=T), args.reps)
+            res["traj_outputs"] = n_out
         else:
             U = torch.empty(prob.dim, prob.dim, dtype=cdt, device="cuda")
             ms = _time(lambda: prop.propagate(prec, out=U), args.reps)
