@@ -126,7 +126,11 @@ typedef enum {
        slice; 1 = the paper's Chebyshev series (Sec. 2.1, Algorithm 1) with one spectral interval
        [-beta, beta] for all slices (beta = largest per-slice norm bound, found on the device) and the
        degree of Eq. error_chebychev; d <= 16 */
-    PARAMENT_OPT_EXP_METHOD = 13
+    PARAMENT_OPT_EXP_METHOD = 13,
+    /* FP32, d <= 16: 1 (default) = one Newton-Schulz step R <- R (3 I - R^dagger R) / 2 on every
+       leaf product (the exact product is unitary; FP32 rounding that repeats from slice to slice
+       otherwise drifts R off the unitary group linearly in the leaf length); 0 = plain products */
+    PARAMENT_OPT_UNITARY_STEP = 14
 } parament_option;
 
 /* per-call diagnostics of the most recent propagate (see parament_get_stats) */

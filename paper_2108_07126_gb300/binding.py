@@ -62,6 +62,7 @@ PARAMENT_OPT_BATCH_LEAF_STEPS = 10
 PARAMENT_OPT_BATCH_ITEMS_PER_SM = 11
 PARAMENT_OPT_BATCH_GRAPH = 12
 PARAMENT_OPT_EXP_METHOD = 13
+PARAMENT_OPT_UNITARY_STEP = 14
 
 PARAMENT_DEV_NONFINITE_NORM = 0x1
 PARAMENT_DEV_NORM_CAPPED = 0x2

@@ -104,6 +104,7 @@ struct parament_ctx {
     bool last_batched = false;
     int64_t opt_batch_leaf = 0, opt_batch_items = 0, opt_batch_graph = 1;
     int64_t opt_exp_method = 0;
+    int64_t opt_unitary_step = 1;
     Workspace cheb;  // Chebyshev pre-pass: max norm bound, degree, 1/beta, coefficients
     int nb_eff = 0;
     std::vector<short> slot_of;
@@ -984,6 +985,7 @@ int forward_setup(parament_ctx *ctx, int fp64, void *U_dst, FusedParams &p, int 
     p.counters = (unsigned long long *)ctx->counters.ptr;
     p.status = (unsigned *)ctx->status.ptr;
     p.extra_squarings = (int)ctx->opt_extra_sq;
+    p.unitary_step = fp64 ? 0 : (int)ctx->opt_unitary_step;
     return PARAMENT_OK;
 }
 
@@ -1426,6 +1428,9 @@ int parament_set_option(parament_ctx *ctx, int key, int64_t value) {
             if (value != 0 && value != 1) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "exp method is 0 or 1");
             ctx->opt_exp_method = value;
             return PARAMENT_OK;
+        case PARAMENT_OPT_UNITARY_STEP:
+            ctx->opt_unitary_step = value != 0;
+            return PARAMENT_OK;
     }
     return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown option key %d", key);
 }
@@ -1445,6 +1450,7 @@ int parament_get_option(const parament_ctx *ctx, int key, int64_t *value) {
         case PARAMENT_OPT_BATCH_ITEMS_PER_SM: *value = ctx->opt_batch_items; return PARAMENT_OK;
         case PARAMENT_OPT_BATCH_GRAPH: *value = ctx->opt_batch_graph; return PARAMENT_OK;
         case PARAMENT_OPT_EXP_METHOD: *value = ctx->opt_exp_method; return PARAMENT_OK;
+        case PARAMENT_OPT_UNITARY_STEP: *value = ctx->opt_unitary_step; return PARAMENT_OK;
     }
     return PARAMENT_ERR_INVALID_VALUE;
 }
@@ -1702,6 +1708,7 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
         p.counters = (unsigned long long *)ctx->bcounters.ptr + (size_t)i * 8;
         p.status = (unsigned *)ctx->bstatus.ptr + (size_t)i * 2;
         p.extra_squarings = (int)ctx->opt_extra_sq;
+        p.unitary_step = fp64 ? 0 : (int)ctx->opt_unitary_step;
         p.warps = ctx->b_warps[i];
         npart += (size_t)nblk_of[i] * Dp[i] * Dp[i];
         ntick += 2 * (size_t)nblk_of[i] + 2;

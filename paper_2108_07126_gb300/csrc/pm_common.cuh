@@ -70,6 +70,7 @@ struct FusedParams {
     unsigned long long *counters;
     unsigned *status;
     int extra_squarings;
+    int unitary_step;          // FP32: one Newton-Schulz step R <- R (3 I - R^dagger R) / 2 on every leaf product
     int warps;                 // warps of a block that own leaves (0 = all; the others only join the barriers)
     const int *cheb_m;         // Chebyshev mode: degree, 1 / beta and coefficients (device, written by
     const double *cheb_inv_beta;  //   cheb_coef_kernel)

@@ -19,6 +19,8 @@
 // operand, X^2, X^3, leaf product R), the coefficient tile and class tile.
 #pragma once
 
+#include <type_traits>
+
 #include "pm_common.cuh"
 
 namespace pm {
@@ -608,6 +610,44 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
 
     // trajectory mode: the forward pass already combined the leaves and recorded statistics
     if constexpr (EXPM == 2) return;
+
+    // ---- FP32: pull the leaf product back towards the unitary group.  The slices of a
+    //      drift-dominated run repeat nearly the same rounding errors, so the deviation of
+    //      R^dagger R from I grows linearly along a leaf; one Newton-Schulz step of the polar
+    //      iteration, R <- R (3 I - R^dagger R) / 2, squares it away (the exact product is unitary).
+    if constexpr (std::is_same<Real, float>::value) {
+        if (p.unitary_step && active_warp) {
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int c = 0; c < TC; ++c) {
+                    const int i = rb + r * G::RBN, jj = G::col(cb, c);
+                    const C v = SR[i * LD + jj];
+                    S1[jj * LD + i] = Cx<Real>::make(v.x, -v.y);  // R^dagger
+                }
+            __syncwarp();
+            C m[TR][TC];
+            mm_tile<Real, D>(S1, SR, rb, cb, m);  // R^dagger R
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int c = 0; c < TC; ++c) {
+                    const bool diag = (rb + r * G::RBN) == G::col(cb, c);
+                    m[r][c] = Cx<Real>::make((diag ? Real(3) : Real(0)) - m[r][c].x, -m[r][c].y);
+                }
+            st_tile<Real, D>(S2, rb, cb, m);
+            __syncwarp();
+            mm_tile<Real, D>(SR, S2, rb, cb, m);  // R (3 I - R^dagger R)
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int c = 0; c < TC; ++c) m[r][c] = Cx<Real>::make(Real(0.5) * m[r][c].x, Real(0.5) * m[r][c].y);
+            st_tile<Real, D>(SR, rb, cb, m);
+            __syncwarp();
+        }
+    }
 
     // ---- optional: every leaf product in FP64 (checkpoints of the adjoint pass)
     if (p.leaf_out && active_warp) {

@@ -169,6 +169,7 @@ extern "C" int parament_propagate_noalloc(int dim, int n_ctrl, const void *H0, c
     p.counters = (unsigned long long *)(base + kOffCnt);
     p.status = (unsigned *)(base + kOffStat);
     p.extra_squarings = 0;
+    p.unitary_step = fp64 ? 0 : 1;  // as parament_propagate with its default options
     NA_CUDA(pm::fused_launch(Dp, fp64, (int)integrator, p, (int)grid, warps, smem, stream));
 #undef NA_CUDA
     (void)DD;

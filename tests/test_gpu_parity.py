@@ -331,6 +331,24 @@ def test_coupled_spins_slice_of_run(prop):
     assert np.max(np.abs(U32 - ref32(full))) <= tol32(16, full.n_steps)
 
 
+def test_fp32_unitary_step_removes_coherent_drift(prop):
+    """Coupled spins, 2^18 slices: repeated FP32 rounding drifts U off the unitary group; one
+    Newton-Schulz step per leaf product (the default) keeps it unitary and closer to the oracle."""
+    from paper_2108_07126_gb300 import binding as b
+
+    prob = wl.coupled_spins(n_steps=1 << 18)
+    I = np.eye(16)
+    out = {}
+    for step in (0, 1):
+        prop.set_option(b.PARAMENT_OPT_UNITARY_STEP, step)
+        U = run(prop, prob, "fp32")
+        out[step] = (np.max(np.abs(U.conj().T @ U - I)), U)
+    U64 = run(prop, prob, "fp64")
+    e0, e1 = (np.max(np.abs(out[s][1] - U64)) for s in (0, 1))
+    assert out[1][0] < 1e-4 < out[0][0]
+    assert e1 < e0 <= tol32(16, prob.n_steps)
+
+
 # --- the paper's Chebyshev exponential (Sec. 2.1, Algorithm 1) ------------------------------------
 
 
