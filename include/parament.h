@@ -127,9 +127,10 @@ typedef enum {
        [-beta, beta] for all slices (beta = largest per-slice norm bound, found on the device) and the
        degree of Eq. error_chebychev; d <= 16 */
     PARAMENT_OPT_EXP_METHOD = 13,
-    /* FP32, d <= 16: 1 (default) = one Newton-Schulz step R <- R (3 I - R^dagger R) / 2 on every
-       leaf product (the exact product is unitary; FP32 rounding that repeats from slice to slice
-       otherwise drifts R off the unitary group linearly in the leaf length); 0 = plain products */
+    /* FP32 and tensor-core precisions: 1 (default) = one Newton-Schulz step R <- R (3 I - R^dagger R) / 2
+       on every leaf product (the exact product is unitary; FP32 rounding that repeats from slice to
+       slice, and the truncating tensor-core accumulation, otherwise drift R off the unitary group
+       linearly in the leaf length); 0 = plain products */
     PARAMENT_OPT_UNITARY_STEP = 14
 } parament_option;
 
@@ -153,6 +154,7 @@ typedef struct {
 
 #define PARAMENT_DEV_NONFINITE_NORM 0x1u /* a slice's norm bound was NaN/Inf */
 #define PARAMENT_DEV_NORM_CAPPED 0x2u    /* a norm exceeded the largest scaling in the table */
+#define PARAMENT_DEV_TENSOR_TIMEOUT 0x4u /* a bounded tensor-core wait gave up; the result is invalid */
 
 /* Library version as major * 1000 + minor. */
 int parament_version(void);

@@ -38,7 +38,7 @@ PM_DECL_D(16)
 #define PM_DECL_L(D)                                                                                     \
     cudaError_t large_dispatch_d##D(int, int, const FusedParams &, void *, int, size_t, cudaStream_t, int); \
     int large_blocks_per_sm_d##D(int, int, size_t, int);                                                 \
-    size_t large_smem_d##D(int, int);
+    size_t large_smem_d##D(int, int, int);
 PM_DECL_L(32)
 PM_DECL_L(64)
 PM_DECL_L(128)
@@ -602,11 +602,11 @@ int large_blocks_per_sm(int Dp, int fp64, int integ, size_t smem, int tc) {
     return memo_occupancy(1, Dp, fp64, integ, 8, smem, tc,
                           [&] { return large_blocks_per_sm_uncached(Dp, fp64, integ, smem, tc); });
 }
-size_t large_smem(int Dp, int fp64, int nb) {
+size_t large_smem(int Dp, int fp64, int nb, int tc = 0) {
     switch (Dp) {
-        case 32: return large_smem_d32(fp64, nb);
-        case 64: return large_smem_d64(fp64, nb);
-        case 128: return large_smem_d128(fp64, nb);
+        case 32: return large_smem_d32(fp64, nb, tc);
+        case 64: return large_smem_d64(fp64, nb, tc);
+        case 128: return large_smem_d128(fp64, nb, tc);
     }
     return 0;
 }
@@ -933,7 +933,7 @@ int forward_setup(parament_ctx *ctx, int fp64, void *U_dst, FusedParams &p, int 
     if (Dp > kMaxSmallDim) {
         // one thread block (256 threads) per leaf; working matrices in a per-block scratch region
         warps = 8;
-        smem = large_smem(Dp, fp64, nb);
+        smem = large_smem(Dp, fp64, nb, tc);
         if (smem > ctx->smem_optin) return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "large-d shared memory %zu B", smem);
         const int bps = large_blocks_per_sm(Dp, fp64, (int)ctx->integ, smem, tc);
         if (bps <= 0) return set_err(ctx, PARAMENT_ERR_CUDA, "occupancy query failed (large d)");

@@ -44,6 +44,7 @@ __host__ __device__ inline int cls_pack(int m, int q, int r, int s) { return m |
 // device status bits (mirrors PARAMENT_DEV_* in parament.h)
 constexpr unsigned kDevNonfinite = 0x1u;
 constexpr unsigned kDevCapped = 0x2u;
+constexpr unsigned kDevTimeout = 0x4u;  // a bounded tensor-core wait gave up: the result is invalid
 
 enum Integrator { kMidpoint = 0, kGL2 = 1, kSimpson = 2 };
 

@@ -14,6 +14,7 @@
 #include <type_traits>
 
 #include "pm_fused.cuh"
+#include "pm_umma.cuh"
 
 namespace pm {
 
@@ -46,18 +47,20 @@ template <typename Real, int D> struct LGeo {
 
 template <int D> struct TcGeo;
 
-template <typename Real, int D>
+// TCM: 0 = CUDA-core products, 1 = 3xTF32 with mma.sync, 2 = 3xTF32 with tcgen05 (D = 128)
+template <typename Real, int D, int TCM = 0>
 __host__ __device__ inline size_t large_panel_bytes() {
     // the FP64 top tree and the tensor-core products run through the same panels
     size_t b = LGeo<Real, D>::PANEL_BYTES;
     if (LGeo<double, D>::PANEL_BYTES > b) b = LGeo<double, D>::PANEL_BYTES;
     if (TcGeo<D>::PANEL_BYTES > b) b = TcGeo<D>::PANEL_BYTES;
+    if (TCM == 2 && umma::kSmemBytes > b) b = umma::kSmemBytes;
     return b;
 }
 
-template <typename Real, int D>
+template <typename Real, int D, int TCM = 0>
 __host__ __device__ inline size_t large_smem_bytes(int n_basis) {
-    size_t b = large_panel_bytes<Real, D>() + (size_t)(n_basis + 1) * sizeof(Real) + 64;
+    size_t b = large_panel_bytes<Real, D, TCM>() + (size_t)(n_basis + 1) * sizeof(Real) + 64;
     return (b + 15) & ~(size_t)15;
 }
 
@@ -287,31 +290,39 @@ __device__ void cta_mm_tc(const float2 *__restrict__ A, const float2 *__restrict
     __syncthreads();
 }
 
-// the complex product used by the large kernel: CUDA cores, or 3xTF32 tensor cores (FP32 only)
-template <typename Real, int D, bool TC>
+// the complex product used by the large kernel: CUDA cores, or 3xTF32 on the tensor cores
+// (FP32 only): mma.sync (TCM = 1) or tcgen05 with tensor-memory accumulators (TCM = 2, D = 128)
+template <typename Real, int D, int TCM>
 __device__ __forceinline__ void large_mm(const typename Cx<Real>::T *A, const typename Cx<Real>::T *B,
-                                         typename Cx<Real>::T *Cout, unsigned char *panels) {
-    if constexpr (TC && std::is_same<Real, float>::value) cta_mm_tc<D>(A, B, Cout, panels);
+                                         typename Cx<Real>::T *Cout, unsigned char *panels, umma::Ctx *uc) {
+    if constexpr (TCM == 2 && D == 128 && std::is_same<Real, float>::value) umma::cmul128(A, B, Cout, panels, *uc);
+    else if constexpr (TCM >= 1 && std::is_same<Real, float>::value) cta_mm_tc<D>(A, B, Cout, panels);
     else cta_mm<Real, D>(A, B, Cout, panels);
 }
 
 // One leaf (slices [N blk / nblk, N (blk + 1) / nblk)) of one problem by one
 // thread block; writes the leaf product to p.partials[blk] (FP64).
 // ws: this block's 6 D x D scratch matrices.
-template <typename Real, int D, int INTEG, bool TC>
+template <typename Real, int D, int INTEG, int TCM>
 __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Real>::T *ws, int blk, int nblk,
-                                           unsigned char *smem) {
+                                           unsigned char *smem, umma::Ctx *uc = nullptr) {
     using G = LGeo<Real, D>;
     using C = typename G::C;
     constexpr int DD = G::DD;
 
     __shared__ int s_code;
     unsigned char *panels = smem;
-    Real *gam = (Real *)(smem + large_panel_bytes<Real, D>());
+    Real *gam = (Real *)(smem + large_panel_bytes<Real, D, TCM>());
     const int tid = threadIdx.x, nb = p.n_basis;
 
-    C *SX = ws, *SX2 = ws + DD, *SX3 = ws + 2 * DD, *SR = ws + 3 * DD, *P0 = ws + 4 * DD, *P1 = ws + 5 * DD;
-    Real *gpk = (Real *)P0;  // packed exponent scratch, free once X is formed
+    C *SX = ws, *SX2 = ws + DD, *SX3 = ws + 2 * DD;
+    // leaf product and the two Horner / squaring buffers rotate through the last three slots
+    C *SR = ws + 3 * DD, *P0 = ws + 4 * DD, *P1 = ws + 5 * DD;
+    // packed exponent: in shared memory (rows padded to D + 1, conflict-free transposed reads)
+    // when the tensor-core stages leave room, else in a free scratch slot
+    constexpr bool kGpkShared = (TCM == 2);
+    static_assert(DD % (4 * kLargeThreads) == 0, "element passes take four elements per thread and step");
+    constexpr int GLD = kGpkShared ? D + 1 : D;
     const Real *packed = (const Real *)p.packed;
 
     const int64_t j0 = p.n_steps * blk / nblk;
@@ -334,69 +345,117 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
         const int code = s_code;
         const int q = cls_q(code), rh = cls_r(code), s = cls_s(code) + p.extra_squarings;
         const Real sc = pow2neg<Real>(s);
+        Real *gpk = kGpkShared ? (Real *)panels : (Real *)P0;
 
-        // packed exponent, then A = -i G / 2^s into SX
-        for (int e = tid; e < DD; e += kLargeThreads) {
-            Real v = 0;
-            for (int b = 0; b < nb; ++b) v = fma(gam[b], __ldg(packed + (size_t)b * DD + e), v);
-            gpk[e] = v;
+        // packed exponent sum_b gamma_b P_b, four entries per thread and step (independent loads)
+        for (int e4 = tid; e4 < DD / 4; e4 += kLargeThreads) {
+            Real v[4] = {Real(0), Real(0), Real(0), Real(0)};
+            for (int b = 0; b < nb; ++b) {
+                Real w[4];
+                ld4<Real>(packed + (size_t)b * DD + 4 * e4, w);
+                const Real g = gam[b];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = fma(g, w[u], v[u]);
+            }
+            const int i = (4 * e4) / D, jj = (4 * e4) % D;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) gpk[i * GLD + jj + u] = v[u];
         }
         __syncthreads();
+        // Hermitian unpack into A = -i G / 2^s (upper triangle: Re, strict lower: Im)
         for (int e = tid; e < DD; e += kLargeThreads) {
             const int i = e / D, jj = e % D;
-            const Real a = gpk[i * D + jj], b = gpk[jj * D + i];
+            const Real a = gpk[i * GLD + jj], b = gpk[jj * GLD + i];
             const Real re = (i <= jj) ? a : b;
             const Real im = (i > jj) ? a : ((i < jj) ? -b : Real(0));
             SX[e] = Cx<Real>::make(im * sc, -re * sc);
         }
         __syncthreads();
-        if (q >= 2) large_mm<Real, D, TC>(SX, SX, SX2, panels);
-        if (q >= 3) large_mm<Real, D, TC>(SX2, SX, SX3, panels);
+        if (q >= 2) large_mm<Real, D, TCM>(SX, SX, SX2, panels, uc);
+        if (q >= 3) large_mm<Real, D, TCM>(SX2, SX, SX3, panels, uc);
         const C *Xq = (q == 1) ? SX : ((q == 2) ? SX2 : SX3);
-        // Horner over blocks with two ping-pong buffers P0 / P1:
+        // Horner over blocks with two ping-pong buffers:
         //   T = a_{q r} X^q + B_{r-1};  T <- X^q T + B_b;  B_b = sum_{l<q} a_{q b + l} X^l
+        // (four elements per thread and step: all loads before the stores, T may alias src)
         auto add_block = [&](C *T, const C *src, Real scale, int b) {
             const Real a0 = coef<Real>(p, q * b);
             const Real a1 = (q >= 2) ? coef<Real>(p, q * b + 1) : Real(0);
             const Real a2 = (q >= 3) ? coef<Real>(p, q * b + 2) : Real(0);
-            for (int e = tid; e < DD; e += kLargeThreads) {
-                C v = src[e];
-                v.x *= scale;
-                v.y *= scale;
-                v.x += ((e / D) == (e % D)) ? a0 : Real(0);
-                if (q >= 2) {
-                    const C x = SX[e];
-                    v.x = fma(a1, x.x, v.x);
-                    v.y = fma(a1, x.y, v.y);
+            for (int e0 = tid; e0 < DD; e0 += 4 * kLargeThreads) {
+                C v[4], x1[4], x2[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = e0 + u * kLargeThreads;
+                    v[u] = src[e];
+                    if (q >= 2) x1[u] = SX[e];
+                    if (q >= 3) x2[u] = SX2[e];
                 }
-                if (q >= 3) {
-                    const C x = SX2[e];
-                    v.x = fma(a2, x.x, v.x);
-                    v.y = fma(a2, x.y, v.y);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = e0 + u * kLargeThreads;
+                    C w = Cx<Real>::make(v[u].x * scale, v[u].y * scale);
+                    w.x += ((e / D) == (e % D)) ? a0 : Real(0);
+                    if (q >= 2) {
+                        w.x = fma(a1, x1[u].x, w.x);
+                        w.y = fma(a1, x1[u].y, w.y);
+                    }
+                    if (q >= 3) {
+                        w.x = fma(a2, x2[u].x, w.x);
+                        w.y = fma(a2, x2[u].y, w.y);
+                    }
+                    T[e] = w;
                 }
-                T[e] = v;
             }
             __syncthreads();
         };
         C *cur = P0, *nxt = P1;
         add_block(cur, Xq, coef<Real>(p, q * rh), rh - 1);
         for (int b = rh - 2; b >= 0; --b) {
-            large_mm<Real, D, TC>(Xq, cur, nxt, panels);
+            large_mm<Real, D, TCM>(Xq, cur, nxt, panels, uc);
             add_block(nxt, nxt, Real(1), b);
             C *t2 = cur; cur = nxt; nxt = t2;
         }
         for (int i = 0; i < s; ++i) {
-            large_mm<Real, D, TC>(cur, cur, nxt, panels);
+            large_mm<Real, D, TCM>(cur, cur, nxt, panels, uc);
             C *t2 = cur; cur = nxt; nxt = t2;
         }
-        // leaf product R <- U_j R
-        large_mm<Real, D, TC>(cur, SR, nxt, panels);
-        for (int e = tid; e < DD; e += kLargeThreads) SR[e] = nxt[e];
-        __syncthreads();
+        // leaf product R <- U_j R into the free buffer, which becomes R; the old R slot is free
+        large_mm<Real, D, TCM>(cur, SR, nxt, panels, uc);
+        {
+            C *old = SR;
+            SR = nxt;
+            P0 = cur;
+            P1 = old;
+        }
         if (tid == 0) {
             n_exp += (unsigned long long)((q - 1) + (rh - 1) + s);
             m_max = max(m_max, cls_m(code));
             s_max = max(s_max, s);
+        }
+    }
+
+    // FP32: one Newton-Schulz step of the polar iteration on the leaf product,
+    // R <- R (3 I - R^dagger R) / 2 (the exact product is unitary; repeated rounding, and the
+    // truncating accumulation of the tensor cores, drift R off the unitary group along a leaf)
+    if constexpr (std::is_same<Real, float>::value) {
+        if (p.unitary_step && len > 0) {
+            for (int e = tid; e < DD; e += kLargeThreads) {
+                const C v = SR[(e % D) * D + e / D];
+                P0[e] = Cx<Real>::make(v.x, -v.y);  // R^dagger
+            }
+            __syncthreads();
+            large_mm<Real, D, TCM>(P0, SR, P1, panels, uc);  // R^dagger R
+            for (int e = tid; e < DD; e += kLargeThreads) {
+                const C v = P1[e];
+                P1[e] = Cx<Real>::make(((e / D) == (e % D) ? Real(3) : Real(0)) - v.x, -v.y);
+            }
+            __syncthreads();
+            large_mm<Real, D, TCM>(SR, P1, P0, panels, uc);  // R (3 I - R^dagger R)
+            for (int e = tid; e < DD; e += kLargeThreads) {
+                const C v = P0[e];
+                SR[e] = Cx<Real>::make(Real(0.5) * v.x, Real(0.5) * v.y);
+            }
+            __syncthreads();
         }
     }
 
@@ -422,12 +481,29 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
     __syncthreads();
 }
 
+// products of the standalone large kernel: tcgen05 for FP32 D = 128, mma.sync for smaller D
+template <typename Real, int D, bool TC>
+__host__ __device__ constexpr int large_tcm() {
+    return !TC ? 0 : ((D == 128 && std::is_same<Real, float>::value) ? 2 : 1);
+}
+
 template <typename Real, int D, int INTEG, bool TC = false>
 __global__ void __launch_bounds__(kLargeThreads, 1) large_kernel(const FusedParams p, void *scratch) {
     extern __shared__ __align__(16) unsigned char smem[];
     using C = typename Cx<Real>::T;
-    large_body<Real, D, INTEG, TC>(p, (C *)scratch + (size_t)blockIdx.x * kLargeSlots * D * D, blockIdx.x, gridDim.x,
-                                   smem);
+    constexpr int TCM = large_tcm<Real, D, TC>();
+    C *ws = (C *)scratch + (size_t)blockIdx.x * kLargeSlots * D * D;
+    if constexpr (TCM == 2) {
+        __shared__ __align__(8) uint64_t s_mbar[umma::kStages];
+        __shared__ uint32_t s_tmem;
+        __shared__ int s_abort;
+        umma::Ctx cx;
+        umma::setup(cx, s_mbar, &s_tmem, &s_abort, p.status);
+        large_body<Real, D, INTEG, TCM>(p, ws, blockIdx.x, gridDim.x, smem, &cx);
+        umma::teardown(cx);
+    } else {
+        large_body<Real, D, INTEG, TCM>(p, ws, blockIdx.x, gridDim.x, smem);
+    }
     // the pairwise tree over the block partials runs in tree_level_kernel launches
 }
 

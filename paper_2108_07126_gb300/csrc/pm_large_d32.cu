@@ -50,8 +50,9 @@ int large_blocks_per_sm_d32(int fp64, int integ, size_t smem, int tc) {
     return e == cudaSuccess ? nb : 0;
 }
 
-size_t large_smem_d32(int fp64, int n_basis) {
-    return fp64 ? large_smem_bytes<double, 32>(n_basis) : large_smem_bytes<float, 32>(n_basis);
+size_t large_smem_d32(int fp64, int n_basis, int tc) {
+    if (fp64) return large_smem_bytes<double, 32>(n_basis);
+    return tc ? large_smem_bytes<float, 32, large_tcm<float, 32, true>()>(n_basis) : large_smem_bytes<float, 32>(n_basis);
 }
 
 }  // namespace pm
