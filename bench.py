@@ -39,8 +39,19 @@ SM_COUNT, FP32_LANES, FP64_FMA_PER_SM_CLK = 152, 128, 2
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of fused_small_kernel<float, 16, GL4> from one ncu capture of
 # 2^18 slices (16 921 344 + 0 bytes), scaled per slice: the traffic is the control samples, linear in N
-TRAFFIC_BYTES_PER_SLICE = 16921344 / 262144
-TRAFFIC_NOTE = "ncu capture of 2^18 slices (16.92 MB) scaled to the launch; algorithmic 64 B per slice"
+TRAFFIC_BYTES_PER_SLICE = 16960512 / 262144
+
+
+def _measured_peaks() -> dict:
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+PEAKS = _measured_peaks()
+TRAFFIC_NOTE = "ncu capture of 2^18 slices (16.96 MB) scaled to the launch; algorithmic 64 B per slice"
 
 
 def parse_args():
@@ -322,6 +333,15 @@ def secondary_workloads(torch, b, wl, dev, flush, steps=10, warmup=3):
         fl = flops_per_launch(st)
         d128[prec] = {"steps_per_s": prob.n_steps / (ms * 1e-3), "ms": ms, "algorithmic_tflops": fl / (ms * 1e-3) / 1e12,
                       "max_abs_err_vs_fp64_gpu_N4096": float(np.max(np.abs(res[("small", prec)][1] - U64s)))}
+    # tcgen05 products: three TF32 MMAs per real product (hi hi + hi lo + lo hi), 8 d^3 flops per
+    # complex product; TF32 peak = measured bf16 peak x the nominal TF32 / bf16 ratio (1.1 / 2.25)
+    st = res[("full", "fp32_tc_tf32x3")][2]
+    n_prod = st["exp_products"] + st["tree_products"] + 2 * st["grid_blocks"]  # + Newton-Schulz step per leaf
+    tf32_peak = PEAKS.get("bf16_tflops", 1900.0) * 1.1 / 2.25
+    ach = 3.0 * 8.0 * 128 ** 3 * n_prod / (res[("full", "fp32_tc_tf32x3")][0] * 1e-3) / 1e12
+    d128["fp32_tc_tf32x3"]["roofline"] = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
+                                           "frac": ach / tf32_peak, "kernel": "large_kernel<float, 128, GL4, tcgen05>",
+                                           "peak_note": "TF32 = measured bf16 burst x 1.1 / 2.25 (of measured)"}
     ms, _, st = res[("small", "fp64")]
     d128["fp64"] = {"steps_per_s": small.n_steps / (ms * 1e-3), "ms_N4096": ms,
                     "algorithmic_tflops": flops_per_launch(st) / (ms * 1e-3) / 1e12}
