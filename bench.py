@@ -65,6 +65,9 @@ def parse_args():
     ap.add_argument("--cpu-sample", type=int, default=1 << 16, help="slices in the timed oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the secondary workloads")
+    ap.add_argument("--scaling", action="store_true",
+                    help="re-run the paper's performance experiments (run time vs d and vs N, CPU crossover) "
+                         "instead of the benchmark line")
     return ap.parse_args()
 
 
@@ -470,10 +473,149 @@ def run_ours(args):
     print(json.dumps(line))
 
 
+_SCALING_CPU = """
+import json, sys, time
+sys.path.insert(0, {root!r})
+import oracle
+from paper_2108_07126_gb300 import workloads as wl
+out = []
+for d, n in {cases!r}:
+    prob = wl.random_problem(d, 2, n, "midpoint", seed=20210816 + d, g_norm=0.3)
+    t0 = time.perf_counter()
+    U = oracle.propagate(prob.H0, prob.Hk, prob.c, prob.dt, prob.integrator)
+    out.append([d, n, time.perf_counter() - t0])
+print(json.dumps(out))
+"""
+
+
+def run_scaling(args):
+    """The paper's performance experiments (Sec. 5) on this GPU, synthetic dense input.
+
+    E1 (run time vs matrix size, 80 000 time steps): d = 2 .. 192, FP32 and FP64, controls
+    resident on the device, CUDA events around parament_propagate.  E3 (run time vs time
+    steps for d = 2, 40, 192): end to end through the C ABI from host memory (controls in,
+    U out, one call each, host wall clock), FP32 and FP64, against the FP64 oracle on one
+    host core; the crossover is where the FP64 GPU call becomes faster than the oracle.
+    Input: workloads.random_problem(d, K = 2, N, midpoint, g_norm = 0.3): GUE drift, two GUE
+    controls, Gaussian samples.  Runs that would take more than ~10 s are skipped.
+    """
+    import numpy as np
+    import torch
+
+    from paper_2108_07126_gb300 import binding as b
+    from paper_2108_07126_gb300 import workloads as wl
+
+    dev = torch.device("cuda", 0)
+    prop = b.Propagator(0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2, written between timed calls
+    results = {"e1": [], "e3_gpu": [], "e3_cpu": []}
+
+    def problem(d, n):
+        return wl.random_problem(d, 2, n, "midpoint", seed=20210816 + d, g_norm=0.3)
+
+    def load(prob, prec, device_ctrl=True):
+        cdt = torch.complex128 if prec == "fp64" else torch.complex64
+        prop.set_hamiltonians(torch.as_tensor(prob.H0).to(cdt), torch.as_tensor(prob.Hk).to(cdt), "midpoint")
+        if device_ctrl:
+            rdt = torch.float64 if prec == "fp64" else torch.float32
+            prop.set_controls(torch.as_tensor(prob.c).to(rdt).to(dev), prob.dt, prob.n_steps)
+        return cdt
+
+    # ---- E1: run time vs d at 80 000 time steps
+    n1 = 80000
+    for prec in ("fp32", "fp64"):
+        rate = None
+        for d in (2, 4, 8, 12, 16, 24, 32, 40, 48, 64, 96, 128, 160, 192):
+            n = n1 if (rate is None or n1 / rate < 10.0) else max(256, int(2.0 * rate))
+            prob = problem(d, n)
+            cdt = load(prob, prec)
+            U = torch.empty(d, d, dtype=cdt, device=dev)
+            per = time_launches(torch, lambda: prop.propagate(prec, out=U), 3, 1, flush)
+            ms = statistics.median(per)
+            rate = n / (ms * 1e-3)
+            row = {"d": d, "prec": prec, "n_steps": n, "ms": ms, "steps_per_s": rate,
+                   "ms_for_80000": ms * n1 / n, "extrapolated": n != n1}
+            results["e1"].append(row)
+            print(json.dumps({"e1": row}), flush=True)
+
+    # ---- E3: run time vs N, end to end from host memory, against the oracle
+    grid = (1, 10, 100, 1000, 10000, 100000, 1000000)
+    for d in (2, 40, 192):
+        for prec in ("fp32", "fp64"):
+            rate = None
+            for n in grid:
+                if rate is not None and n / rate > 10.0:
+                    break
+                prob = problem(d, n)
+                cdt = load(prob, prec, device_ctrl=False)
+                rdt = torch.float64 if prec == "fp64" else torch.float32
+                c_host = torch.as_tensor(prob.c).to(rdt).contiguous().pin_memory()
+                U_host = np.zeros((d, d), np.complex128 if prec == "fp64" else np.complex64)
+                pc = b.PARAMENT_PREC_FP64 if prec == "fp64" else b.PARAMENT_PREC_FP32
+                cd = b.PARAMENT_F64 if prec == "fp64" else b.PARAMENT_F32
+
+                def call():
+                    b.parament_set_controls(prop.ctx, c_host.data_ptr(), cd, n, prob.dt)
+                    b.parament_propagate(prop.ctx, U_host.ctypes.data, pc)  # host U: returns after the copy
+
+                call()
+                ts = []
+                for _ in range(5 if n <= 10000 else 2):
+                    t0 = time.perf_counter()
+                    call()
+                    ts.append(time.perf_counter() - t0)
+                sec = statistics.median(ts)
+                rate = n / sec
+                row = {"d": d, "prec": prec, "n_steps": n, "seconds": sec}
+                results["e3_gpu"].append(row)
+                print(json.dumps({"e3_gpu": row}), flush=True)
+    prop.close()
+
+    # CPU side: the FP64 oracle on one host core, in a fresh process, within ~10 s per size
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    for d, cap in ((2, 100000), (40, 10000), (192, 100)):
+        cases = [(d, n) for n in grid if n <= cap]
+        code = _SCALING_CPU.format(root=ROOT, cases=cases)
+        r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+        if r.returncode != 0:
+            raise RuntimeError(r.stderr)
+        for dd, n, sec in json.loads(r.stdout.strip().splitlines()[-1]):
+            row = {"d": dd, "n_steps": n, "seconds": sec, "cores": 1}
+            results["e3_cpu"].append(row)
+            print(json.dumps({"e3_cpu": row}), flush=True)
+
+    # crossover (FP64): first N on the grid where the GPU call beats the oracle, log-log
+    # interpolated between the neighbouring grid points
+    cross = {}
+    for d in (2, 40, 192):
+        g = {r["n_steps"]: r["seconds"] for r in results["e3_gpu"] if r["d"] == d and r["prec"] == "fp64"}
+        c = {r["n_steps"]: r["seconds"] for r in results["e3_cpu"] if r["d"] == d}
+        common = sorted(set(g) & set(c))
+        val = None
+        for i, n in enumerate(common):
+            if g[n] < c[n]:
+                if i == 0:
+                    val = {"n_steps": n, "note": "GPU faster already at the smallest N"}
+                else:
+                    n0 = common[i - 1]
+                    r0 = math.log(g[n0] / c[n0])
+                    r1 = math.log(g[n] / c[n])
+                    x = math.log(n0) + (math.log(n) - math.log(n0)) * r0 / (r0 - r1)
+                    val = {"n_steps": math.exp(x), "between": [n0, n]}
+                break
+        cross[d] = val
+    print(json.dumps({"scaling_summary": {"crossover_fp64": cross, "input": "random_problem(d, 2, N, midpoint, "
+                                          "g_norm=0.3), GUE drift and controls", "cpu": "FP64 oracle, one core"}}))
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.scaling:
+        run_scaling(args)
     else:
         run_ours(args)
 

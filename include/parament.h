@@ -179,7 +179,7 @@ int parament_set_stream(parament_ctx *ctx, void *cuda_stream);
  * and choose the integrator (Sec. 6, Parament_setHamiltonian; the Magnus
  * choice makes the library form the commutator basis here, Sec. 4).
  * `dtype` is the storage type of H0/Hk and of every later U_out.  The data are
- * copied; the caller keeps ownership.  1 <= d <= 128 (PARAMENT_ERR_UNSUPPORTED
+ * copied; the caller keeps ownership.  1 <= d <= 256 (PARAMENT_ERR_UNSUPPORTED
  * above; d is padded with zeros to the next power of two, which is exact),
  * 0 <= K <= 16.  Hk may be NULL when K = 0.
  * Resets any controls set before.  Errors: INVALID_VALUE, NONFINITE,

@@ -33,6 +33,7 @@ SOURCES = [
     "pm_large_d32.cu",
     "pm_large_d64.cu",
     "pm_large_d128.cu",
+    "pm_large_d256.cu",
     "pm_batched_fm.cu",
     "pm_batched_fm_tc.cu",
     "pm_batched_dm.cu",

@@ -42,6 +42,7 @@ PM_DECL_D(16)
 PM_DECL_L(32)
 PM_DECL_L(64)
 PM_DECL_L(128)
+PM_DECL_L(256)
 #undef PM_DECL_L
 cudaError_t batch_basis_launch(int, int, const BatchInst *, const int2 *, int, int, double2 *, void *, double *,
                                cudaStream_t);
@@ -62,7 +63,8 @@ using namespace pm;
 
 namespace {
 
-constexpr int kMaxDim = 128;
+constexpr int kMaxDim = 256;
+constexpr int kMaxBatchDim = 128;  // the batched kernel's block-level bodies go up to D = 128
 constexpr int kMaxSmallDim = 16;  // larger dimensions use one thread block per leaf
 constexpr int kLeafMinSteps = 8;  // fewer blocks for short runs: each leaf gets >= 8 slices
 
@@ -587,6 +589,7 @@ cudaError_t large_dispatch(int Dp, int fp64, int integ, const FusedParams &p, vo
         case 32: return large_dispatch_d32(fp64, integ, p, scratch, grid, smem, st, tc);
         case 64: return large_dispatch_d64(fp64, integ, p, scratch, grid, smem, st, tc);
         case 128: return large_dispatch_d128(fp64, integ, p, scratch, grid, smem, st, tc);
+        case 256: return large_dispatch_d256(fp64, integ, p, scratch, grid, smem, st, tc);
     }
     return cudaErrorInvalidValue;
 }
@@ -595,6 +598,7 @@ int large_blocks_per_sm_uncached(int Dp, int fp64, int integ, size_t smem, int t
         case 32: return large_blocks_per_sm_d32(fp64, integ, smem, tc);
         case 64: return large_blocks_per_sm_d64(fp64, integ, smem, tc);
         case 128: return large_blocks_per_sm_d128(fp64, integ, smem, tc);
+        case 256: return large_blocks_per_sm_d256(fp64, integ, smem, tc);
     }
     return 0;
 }
@@ -607,6 +611,7 @@ size_t large_smem(int Dp, int fp64, int nb, int tc = 0) {
         case 32: return large_smem_d32(fp64, nb, tc);
         case 64: return large_smem_d64(fp64, nb, tc);
         case 128: return large_smem_d128(fp64, nb, tc);
+        case 256: return large_smem_d256(fp64, nb, tc);
     }
     return 0;
 }
@@ -1542,7 +1547,7 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
     if (n == 0) return PARAMENT_OK;
     for (int i = 0; i < n; ++i) {
         const parament_instance &q = inst[i];
-        if (q.dim < 1 || q.dim > kMaxDim || q.n_ctrl < 0 || q.n_ctrl > kMaxControls || q.n_steps < 0 ||
+        if (q.dim < 1 || q.dim > kMaxBatchDim || q.n_ctrl < 0 || q.n_ctrl > kMaxControls || q.n_steps < 0 ||
             q.n_steps > (int64_t)0x7fffffff || !std::isfinite(q.dt))
             return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "instance %d: bad sizes", i);
         const int64_t S = samples_for(q.n_steps, integ);

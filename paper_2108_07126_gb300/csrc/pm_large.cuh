@@ -1,4 +1,4 @@
-// Propagation kernel for padded dimensions D in {32, 64, 128}.
+// Propagation kernel for padded dimensions D in {32, 64, 128, 256}.
 //
 // Same method as the fused small-D kernel (per slice: effective coefficients,
 // FP64 norm bound, exponent assembly, Taylor / Paterson-Stockmeyer on
@@ -29,6 +29,8 @@ template <> struct LargeTile<float, 128> { static constexpr int TR = 4, TC = 4, 
 template <> struct LargeTile<double, 32> { static constexpr int TR = 2, TC = 2, PASS = 1, KP = 8; };
 template <> struct LargeTile<double, 64> { static constexpr int TR = 4, TC = 4, PASS = 1, KP = 8; };
 template <> struct LargeTile<double, 128> { static constexpr int TR = 4, TC = 4, PASS = 4, KP = 8; };
+template <> struct LargeTile<float, 256> { static constexpr int TR = 4, TC = 4, PASS = 16, KP = 16; };
+template <> struct LargeTile<double, 256> { static constexpr int TR = 4, TC = 4, PASS = 16, KP = 8; };
 
 template <typename Real, int D> struct LGeo {
     using T = LargeTile<Real, D>;
@@ -150,6 +152,7 @@ template <int D> struct TcTile;
 template <> struct TcTile<32> { static constexpr int PASS = 1, WM = 2, WN = 4; };
 template <> struct TcTile<64> { static constexpr int PASS = 1, WM = 2, WN = 4; };
 template <> struct TcTile<128> { static constexpr int PASS = 2, WM = 2, WN = 4; };
+template <> struct TcTile<256> { static constexpr int PASS = 8, WM = 2, WN = 4; };
 
 template <int D> struct TcGeo {
     static constexpr int PASS = TcTile<D>::PASS, WM = TcTile<D>::WM, WN = TcTile<D>::WN;

@@ -1,0 +1,58 @@
+// Instantiations of the large-dimension propagation kernel for padded dimension 256.
+#include "pm_large.cuh"
+
+namespace pm {
+
+cudaError_t large_dispatch_d256(int fp64, int integ, const FusedParams &p, void *scratch, int grid, size_t smem,
+                               cudaStream_t st, int tc) {
+    if (tc && !fp64) {
+        switch (integ) {
+            case kMidpoint: return launch_large<float, 256, kMidpoint, true>(p, scratch, grid, smem, st);
+            case kGL2: return launch_large<float, 256, kGL2, true>(p, scratch, grid, smem, st);
+            case kSimpson: return launch_large<float, 256, kSimpson, true>(p, scratch, grid, smem, st);
+        }
+        return cudaErrorInvalidValue;
+    }
+    switch (integ * 2 + (fp64 ? 1 : 0)) {
+        case 0: return launch_large<float, 256, kMidpoint>(p, scratch, grid, smem, st);
+        case 1: return launch_large<double, 256, kMidpoint>(p, scratch, grid, smem, st);
+        case 2: return launch_large<float, 256, kGL2>(p, scratch, grid, smem, st);
+        case 3: return launch_large<double, 256, kGL2>(p, scratch, grid, smem, st);
+        case 4: return launch_large<float, 256, kSimpson>(p, scratch, grid, smem, st);
+        case 5: return launch_large<double, 256, kSimpson>(p, scratch, grid, smem, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int large_blocks_per_sm_d256(int fp64, int integ, size_t smem, int tc) {
+    int nb = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    auto q = [&](auto k) {
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kLargeThreads, smem);
+    };
+    if (tc && !fp64) {
+        switch (integ) {
+            case kMidpoint: q(large_kernel<float, 256, kMidpoint, true>); break;
+            case kGL2: q(large_kernel<float, 256, kGL2, true>); break;
+            case kSimpson: q(large_kernel<float, 256, kSimpson, true>); break;
+        }
+        return e == cudaSuccess ? nb : 0;
+    }
+    switch (integ * 2 + (fp64 ? 1 : 0)) {
+        case 0: q(large_kernel<float, 256, kMidpoint>); break;
+        case 1: q(large_kernel<double, 256, kMidpoint>); break;
+        case 2: q(large_kernel<float, 256, kGL2>); break;
+        case 3: q(large_kernel<double, 256, kGL2>); break;
+        case 4: q(large_kernel<float, 256, kSimpson>); break;
+        case 5: q(large_kernel<double, 256, kSimpson>); break;
+    }
+    return e == cudaSuccess ? nb : 0;
+}
+
+size_t large_smem_d256(int fp64, int n_basis, int tc) {
+    if (fp64) return large_smem_bytes<double, 256>(n_basis);
+    return tc ? large_smem_bytes<float, 256, large_tcm<float, 256, true>()>(n_basis) : large_smem_bytes<float, 256>(n_basis);
+}
+
+}  // namespace pm

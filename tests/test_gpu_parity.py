@@ -210,7 +210,7 @@ def test_state_machine_and_errors(prop, torch):
         Hok = torch.eye(2, dtype=torch.complex128, device="cuda")
         assert b.raw_call("parament_set_hamiltonians", ctx, 0, 0, Hok.data_ptr(), None, 1, 0) == \
             b.PARAMENT_ERR_INVALID_VALUE
-        assert b.raw_call("parament_set_hamiltonians", ctx, 256, 0, Hok.data_ptr(), None, 1, 0) == \
+        assert b.raw_call("parament_set_hamiltonians", ctx, 257, 0, Hok.data_ptr(), None, 1, 0) == \
             b.PARAMENT_ERR_UNSUPPORTED
         assert b.raw_call("parament_set_controls", ctx, None, 1, 4, 0.1) == b.PARAMENT_ERR_STATE
         assert b.raw_call("parament_set_hamiltonians", ctx, 2, 0, Hok.data_ptr(), None, 1, 0) == b.PARAMENT_OK
@@ -248,15 +248,15 @@ def test_mixed_control_dtypes(prop, torch):
 
 
 @pytest.mark.parametrize("integrator", INTEGRATORS)
-@pytest.mark.parametrize("d", [17, 32, 40, 64, 100, 128])
+@pytest.mark.parametrize("d", [17, 32, 40, 64, 100, 128, 192, 256])
 def test_large_d_fp64_matches_oracle(prop, integrator, d):
-    n = 37 if d <= 64 else 9
+    n = 37 if d <= 64 else (9 if d <= 128 else 5)
     prob = wl.random_problem(d, 2, n, integrator, seed=600 + d, g_norm=0.6)
     U = run(prop, prob, "fp64")
     assert np.max(np.abs(U - ref(prob))) <= TOL64
 
 
-@pytest.mark.parametrize("d", [32, 64, 128])
+@pytest.mark.parametrize("d", [32, 64, 128, 192])
 def test_large_d_fp32_matches_oracle(prop, d):
     n = 301 if d <= 64 else 41
     prob = wl.random_problem(d, 3, n, "magnus4_gl2", seed=700 + d, g_norm=0.5)
@@ -264,7 +264,7 @@ def test_large_d_fp32_matches_oracle(prop, d):
     assert np.max(np.abs(U - ref32(prob))) <= tol32(d, n)
 
 
-@pytest.mark.parametrize("d", [32, 64, 128])
+@pytest.mark.parametrize("d", [32, 64, 128, 192])
 def test_tensor_core_tf32x3_matches_oracle(prop, d):
     """3xTF32 tensor-core products keep FP32 accuracy."""
     n = 301 if d <= 64 else 41
