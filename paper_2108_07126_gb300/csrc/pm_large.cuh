@@ -60,9 +60,24 @@ __host__ __device__ inline size_t large_panel_bytes() {
     return b;
 }
 
+// FP32 at D <= 64 on the CUDA cores keeps all six working matrices in shared memory
+// (6 D^2 complex64 = 192 KB at D = 64) instead of the global scratch region.
+template <typename Real, int D, int TCM>
+__host__ __device__ constexpr bool large_resident() {
+    return std::is_same<Real, float>::value && D <= 64 && TCM == 0;
+}
+
+// bytes in front of the coefficient tile: the resident matrices, or the staging panels
+template <typename Real, int D, int TCM = 0>
+__host__ __device__ inline size_t large_front_bytes() {
+    const size_t res = large_resident<Real, D, TCM>() ? (size_t)kLargeSlots * D * D * sizeof(typename Cx<Real>::T) : 0;
+    const size_t pan = large_panel_bytes<Real, D, TCM>();
+    return res > pan ? res : pan;
+}
+
 template <typename Real, int D, int TCM = 0>
 __host__ __device__ inline size_t large_smem_bytes(int n_basis) {
-    size_t b = large_panel_bytes<Real, D, TCM>() + (size_t)(n_basis + 1) * sizeof(Real) + 64;
+    size_t b = large_front_bytes<Real, D, TCM>() + (size_t)(n_basis + 1) * sizeof(Real) + 64;
     return (b + 15) & ~(size_t)15;
 }
 
@@ -293,6 +308,55 @@ __device__ void cta_mm_tc(const float2 *__restrict__ A, const float2 *__restrict
     __syncthreads();
 }
 
+// Cout = A * B for D x D complex64 matrices already in shared memory (row stride D), by the
+// whole block: thread (ty, tx) = (tid / 16, tid % 16) owns rows ty + 16 r and the TC consecutive
+// columns TC tx .. TC tx + TC - 1.  Per pair of k the A reads are two broadcast rows per warp
+// (16-byte loads) and the B reads one contiguous 16 TC-complex row segment.  Cout must not
+// alias A or B; ends with a block barrier.
+template <int D>
+__device__ __forceinline__ void smem_mm(const float2 *__restrict__ A, const float2 *__restrict__ B,
+                                        float2 *__restrict__ Cout) {
+    constexpr int TR = D / 16, TC = D / 16;
+    static_assert(TR * TC * kLargeThreads == D * D && TC % 2 == 0, "thread tiling");
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    float2 acc[TR][TC];
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+        for (int c = 0; c < TC; ++c) acc[r][c] = make_float2(0.f, 0.f);
+#pragma unroll 4
+    for (int k = 0; k < D; k += 2) {
+        float2 a[TR][2], b[2][TC];
+#pragma unroll
+        for (int r = 0; r < TR; ++r) {
+            const float4 v = *reinterpret_cast<const float4 *>(A + (ty + 16 * r) * D + k);
+            a[r][0] = make_float2(v.x, v.y);
+            a[r][1] = make_float2(v.z, v.w);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int c = 0; c < TC; c += 2) {
+                const float4 v = *reinterpret_cast<const float4 *>(B + (k + u) * D + TC * tx + c);
+                b[u][c] = make_float2(v.x, v.y);
+                b[u][c + 1] = make_float2(v.z, v.w);
+            }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                for (int c = 0; c < TC; ++c) cfma(acc[r][c], a[r][u], b[u][c]);
+    }
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+        for (int c = 0; c < TC; c += 2)
+            *reinterpret_cast<float4 *>(Cout + (ty + 16 * r) * D + TC * tx + c) =
+                make_float4(acc[r][c].x, acc[r][c].y, acc[r][c + 1].x, acc[r][c + 1].y);
+    __syncthreads();
+}
+
 // the complex product used by the large kernel: CUDA cores, or 3xTF32 on the tensor cores
 // (FP32 only): mma.sync (TCM = 1) or tcgen05 with tensor-memory accumulators (TCM = 2, D = 128)
 template <typename Real, int D, int TCM>
@@ -300,6 +364,7 @@ __device__ __forceinline__ void large_mm(const typename Cx<Real>::T *A, const ty
                                          typename Cx<Real>::T *Cout, unsigned char *panels, umma::Ctx *uc) {
     if constexpr (TCM == 2 && D == 128 && std::is_same<Real, float>::value) umma::cmul128(A, B, Cout, panels, *uc);
     else if constexpr (TCM >= 1 && std::is_same<Real, float>::value) cta_mm_tc<D>(A, B, Cout, panels);
+    else if constexpr (large_resident<Real, D, TCM>()) smem_mm<D>(A, B, Cout);
     else cta_mm<Real, D>(A, B, Cout, panels);
 }
 
@@ -315,15 +380,17 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
 
     __shared__ int s_code;
     unsigned char *panels = smem;
-    Real *gam = (Real *)(smem + large_panel_bytes<Real, D, TCM>());
+    Real *gam = (Real *)(smem + large_front_bytes<Real, D, TCM>());
     const int tid = threadIdx.x, nb = p.n_basis;
+    constexpr bool kResident = large_resident<Real, D, TCM>();
+    if constexpr (kResident) ws = (C *)smem;  // the working matrices live in shared memory
 
     C *SX = ws, *SX2 = ws + DD, *SX3 = ws + 2 * DD;
     // leaf product and the two Horner / squaring buffers rotate through the last three slots
     C *SR = ws + 3 * DD, *P0 = ws + 4 * DD, *P1 = ws + 5 * DD;
     // packed exponent: in shared memory (rows padded to D + 1, conflict-free transposed reads)
     // when the tensor-core stages leave room, else in a free scratch slot
-    constexpr bool kGpkShared = (TCM == 2);
+    constexpr bool kGpkShared = (TCM == 2) || kResident;
     static_assert(DD % (4 * kLargeThreads) == 0, "element passes take four elements per thread and step");
     constexpr int GLD = kGpkShared ? D + 1 : D;
     const Real *packed = (const Real *)p.packed;
@@ -348,7 +415,7 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
         const int code = s_code;
         const int q = cls_q(code), rh = cls_r(code), s = cls_s(code) + p.extra_squarings;
         const Real sc = pow2neg<Real>(s);
-        Real *gpk = kGpkShared ? (Real *)panels : (Real *)P0;
+        Real *gpk = (TCM == 2) ? (Real *)panels : (Real *)P0;  // resident: the free slot P0 in shared memory
 
         // packed exponent sum_b gamma_b P_b, four entries per thread and step (independent loads)
         for (int e4 = tid; e4 < DD / 4; e4 += kLargeThreads) {
