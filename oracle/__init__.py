@@ -9,6 +9,7 @@ from .parament_oracle import (  # noqa: F401
     commutator,
     effective_control_count,
     exact_slice_propagators,
+    exponent_derivatives,
     frechet_exp,
     frechet_phi,
     gate_loss,

@@ -35,9 +35,10 @@ What it computes, each piece following the paper's definitions:
   form of the Schroedinger equation); a plain sequential left-multiplication
   in time order.
 * ``loss_and_gradient``  -- gate-fidelity loss L = 1 - |Tr(V^dagger U)|^2 / d^2 and
-  dL/dc_k(t_j) for the midpoint rule, with the Frechet derivative of exp taken
-  from the Daleckii-Krein formula (Sec. 7 motivates the gradient for GRAPE;
-  the paper itself gives no gradient formula).
+  dL/dc_k(s) for every control sample and every integrator (chain rule through
+  the exponent formulas, ``exponent_derivatives``), with the Frechet derivative
+  of exp taken from the Daleckii-Krein formula (Sec. 7 motivates the gradient
+  for GRAPE; the paper itself gives no gradient formula).
 
 All arithmetic is complex128 / float64.  Parity is pinned by the tests in
 ``tests/test_oracle_pins.py`` (closed forms, convergence orders, brute-force
@@ -217,26 +218,69 @@ def frechet_exp(G: np.ndarray, E: np.ndarray) -> np.ndarray:
     return Q @ ((Qh @ E @ Q) * frechet_phi(lam)) @ Qh
 
 
-def loss_and_gradient(H0, Hk, c, dt: float, V, integrator: str = MIDPOINT):
-    """Loss L, gradient dL/dc (K, N) and U(T) for the midpoint rule.
+def exponent_derivatives(H0, Hk, c, dt: float, integrator: str):
+    """dG_j / dc_k(s) for every slice j, control k and sample s the slice reads.
 
-    U = S_j U_j P_{j-1} with the exclusive prefix P_{j-1} = U_{j-1} ... U_1
-    and suffix S_j = U_N ... U_{j+1}; with z = Tr(V^dagger U),
-    dz/dc_kj = Tr(Lambda_j L_{X_j}(E_k)), Lambda_j = P_{j-1} V^dagger S_j,
-    X_j = -i G_j, E_k = dX_j/dc_kj = -i dt H_k, and
-    dL/dc_kj = -(2/d^2) Re(conj(z) dz/dc_kj).
+    Returns a list of (offset, D) with D of shape (N, K, d, d): D[j, k] is the derivative of
+    G_j with respect to the sample at index offset + 2 j (offset + j for the midpoint rule)
+    of control k, from the exponent formulas of ``slice_exponents`` (Sec. 4, Eq. magnus):
+      midpoint    G = dt H                              dG/dc_k = dt H_k
+      GL4         G = dt/2 (H1 + H2) + i w [H1, H2],    w = sqrt(3) dt^2 / 12
+                  dG/dc1_k = dt/2 H_k + i w [H_k, H2],  dG/dc2_k = dt/2 H_k + i w [H1, H_k]
+      Simpson     G = dt/6 (H1 + 4 H2 + H3) + i (dt^2/12) [H1, H3]
+                  dG/dc1_k = dt/6 H_k + i (dt^2/12) [H_k, H3],  dG/dc2_k = 4 dt/6 H_k,
+                  dG/dc3_k = dt/6 H_k + i (dt^2/12) [H1, H_k]
     """
-    if integrator != MIDPOINT:
-        raise NotImplementedError("the oracle gradient covers the midpoint rule")
     H0 = np.asarray(H0, dtype=np.complex128)
     d = H0.shape[0]
     Hk = np.asarray(Hk, dtype=np.complex128).reshape(-1, d, d)
     K = Hk.shape[0]
     c = np.asarray(c, dtype=np.float64).reshape(K, -1)
-    N = c.shape[1]
+    S = c.shape[1]
+    if integrator == MIDPOINT:
+        N = S
+        return [(0, np.broadcast_to(dt * Hk[None], (N, K, d, d)))]
+    if integrator == MAGNUS4_GL2:
+        N = S // 2
+        H1 = hamiltonian(H0, Hk, c[:, 0::2])[:, None]      # (N, 1, d, d)
+        H2 = hamiltonian(H0, Hk, c[:, 1::2])[:, None]
+        w = math.sqrt(3.0) * dt * dt / 12.0
+        Hb = Hk[None]                                       # (1, K, d, d)
+        D1 = 0.5 * dt * Hb + 1j * w * commutator(Hb, H2)
+        D2 = 0.5 * dt * Hb + 1j * w * commutator(H1, Hb)
+        return [(0, D1), (1, D2)]
+    if integrator == MAGNUS4_SIMPSON:
+        N = (S - 1) // 2
+        H1 = hamiltonian(H0, Hk, c[:, 0:S - 1:2])[:, None]
+        H3 = hamiltonian(H0, Hk, c[:, 2:S:2])[:, None]
+        w = dt * dt / 12.0
+        Hb = np.broadcast_to(Hk[None], (N, K, d, d))
+        D1 = dt / 6.0 * Hb + 1j * w * commutator(Hk[None], H3)
+        D2 = 4.0 * dt / 6.0 * Hb
+        D3 = dt / 6.0 * Hb + 1j * w * commutator(H1, Hk[None])
+        return [(0, D1), (1, D2), (2, D3)]
+    raise ValueError(f"unknown integrator {integrator!r}")
+
+
+def loss_and_gradient(H0, Hk, c, dt: float, V, integrator: str = MIDPOINT):
+    """Loss L, gradient dL/dc (K, S) over the control samples, and U(T).
+
+    U = S_j U_j P_{j-1} with the exclusive prefix P_{j-1} = U_{j-1} ... U_1
+    and suffix S_j = U_N ... U_{j+1}; with z = Tr(V^dagger U) and X_j = -i G_j,
+    dz/dc = sum_j Tr(Lambda_j L_{X_j}(dX_j/dc)), Lambda_j = P_{j-1} V^dagger S_j,
+    dX_j/dc = -i dG_j/dc (``exponent_derivatives``: one sample enters one slice, or two
+    neighbouring slices for the shared Simpson end points), and
+    dL/dc = -(2/d^2) Re(conj(z) dz/dc).
+    """
+    H0 = np.asarray(H0, dtype=np.complex128)
+    d = H0.shape[0]
+    Hk = np.asarray(Hk, dtype=np.complex128).reshape(-1, d, d)
+    K = Hk.shape[0]
+    c = np.asarray(c, dtype=np.float64).reshape(K, -1)
     V = np.asarray(V, dtype=np.complex128)
 
-    G = slice_exponents(H0, Hk, c, dt, MIDPOINT)
+    G = slice_exponents(H0, Hk, c, dt, integrator)
+    N = G.shape[0]
     lam, Q = np.linalg.eigh(G)
     Qh = np.conj(np.swapaxes(Q, -1, -2))
     Uj = (Q * np.exp(-1j * lam)[:, None, :]) @ Qh
@@ -257,12 +301,17 @@ def loss_and_gradient(H0, Hk, c, dt: float, V, integrator: str = MIDPOINT):
     z = np.trace(np.conj(V).T @ U)
     loss = float(1.0 - abs(z) ** 2 / d ** 2)
     Lam = P @ np.conj(V).T @ S                       # (N, d, d)
-    E = -1j * dt * Hk                                # (K, d, d)
     # Tr(Lam L_X(E)) = sum_ab (Q^dag Lam Q)_ba (Q^dag E Q)_ab Phi_ab
     Lt = Qh @ Lam @ Q                                # (N, d, d)
-    Et = np.einsum("nab,kbc,ncd->nkad", Qh, E, Q)    # (N, K, d, d)
     phi = frechet_phi(lam)                           # (N, d, d)
-    dz = np.einsum("nba,nkab,nab->kn", Lt, Et, phi)  # (K, N)
+    dz = np.zeros(c.shape, dtype=np.complex128)      # (K, S)
+    step = 1 if integrator == MIDPOINT else 2
+    for off, Dg in exponent_derivatives(H0, Hk, c, dt, integrator):
+        E = -1j * np.asarray(Dg)                     # (N, K, d, d)
+        Et = np.einsum("nab,nkbc,ncd->nkad", Qh, E, Q)
+        dzr = np.einsum("nba,nkab,nab->kn", Lt, Et, phi)  # (K, N)
+        for j in range(N):
+            dz[:, off + step * j] += dzr[:, j]
     grad = -(2.0 / d ** 2) * np.real(np.conj(z) * dz)
     return loss, grad, U
 

@@ -298,15 +298,15 @@ def test_effective_control_count():
 # --- gradient -----------------------------------------------------------------------------
 
 
-def _fd_gradient(prob, V, h, entries):
+def _fd_gradient(prob, V, h, entries, integrator="midpoint"):
     out = []
     for (k, j) in entries:
         cp = prob.c.copy()
         cm = prob.c.copy()
         cp[k, j] += h
         cm[k, j] -= h
-        Lp = oracle.gate_loss(oracle.propagate(prob.H0, prob.Hk, cp, prob.dt, "midpoint"), V)
-        Lm = oracle.gate_loss(oracle.propagate(prob.H0, prob.Hk, cm, prob.dt, "midpoint"), V)
+        Lp = oracle.gate_loss(oracle.propagate(prob.H0, prob.Hk, cp, prob.dt, integrator), V)
+        Lm = oracle.gate_loss(oracle.propagate(prob.H0, prob.Hk, cm, prob.dt, integrator), V)
         out.append((Lp - Lm) / (2 * h))
     return np.array(out)
 
@@ -352,6 +352,55 @@ def test_gradient_workload_subset_matches_fd():
     fd = _fd_gradient(prob, prob.V, 1e-6, entries)
     g = np.array([grad[k, j] for (k, j) in entries])
     assert np.max(np.abs(g - fd)) <= 1e-6 * np.max(np.abs(fd))
+
+
+@pytest.mark.parametrize("integrator", ["magnus4_gl2", "magnus4_simpson"])
+def test_magnus_gradient_matches_finite_differences(integrator):
+    # every sample of a short run, including the Simpson end points shared by two slices
+    rng = np.random.default_rng(21)
+    prob = wl.random_problem(3, 2, 7, integrator, seed=21, g_norm=0.5)
+    V = wl.haar_unitary(rng, 3)
+    loss, grad, U = oracle.loss_and_gradient(prob.H0, prob.Hk, prob.c, prob.dt, V, integrator)
+    assert grad.shape == prob.c.shape
+    assert abs(loss - oracle.gate_loss(oracle.propagate(prob.H0, prob.Hk, prob.c, prob.dt, integrator), V)) < 1e-14
+    entries = [(k, s) for k in range(2) for s in range(prob.c.shape[1])]
+    fd = _fd_gradient(prob, V, 1e-6, entries, integrator)
+    g = np.array([grad[k, s] for (k, s) in entries])
+    assert np.max(np.abs(g - fd)) <= 1e-6 * np.max(np.abs(fd))
+
+
+def test_magnus_gradient_reduces_to_midpoint_for_equal_nodes():
+    # GL4 with c1 = c2 per slice: the commutator term and its derivative vanish, G = dt H, and
+    # dL/dc1 + dL/dc2 equals the midpoint gradient of the same piecewise-constant controls
+    rng = np.random.default_rng(22)
+    mid = wl.random_problem(4, 2, 9, "midpoint", seed=22, g_norm=0.4)
+    c2 = np.repeat(mid.c, 2, axis=1)
+    V = wl.haar_unitary(rng, 4)
+    _, g_mid, U_mid = oracle.loss_and_gradient(mid.H0, mid.Hk, mid.c, mid.dt, V, "midpoint")
+    _, g_gl, U_gl = oracle.loss_and_gradient(mid.H0, mid.Hk, c2, mid.dt, V, "magnus4_gl2")
+    assert np.max(np.abs(U_mid - U_gl)) < 1e-13
+    assert np.max(np.abs(g_gl[:, 0::2] + g_gl[:, 1::2] - g_mid)) < 1e-13
+
+
+def test_planted_commutator_derivative_sign_fails_fd(monkeypatch):
+    # a sign slip in the derivative of the Omega_2 term (i w [H_k, H2] -> -i w [H_k, H2])
+    real = orc.exponent_derivatives
+
+    def planted(H0, Hk, c, dt, integrator):
+        out = real(H0, Hk, c, dt, integrator)
+        Hk_ = np.asarray(Hk, dtype=np.complex128)
+        return [(off, 2 * (0.5 * dt) * Hk_[None] - D) if off == 0 else (off, D) for off, D in out]
+
+    monkeypatch.setattr(orc, "exponent_derivatives", planted)
+    rng = np.random.default_rng(23)
+    prob = wl.random_problem(3, 2, 5, "magnus4_gl2", seed=23, g_norm=0.8)
+    V = wl.haar_unitary(rng, 3)
+    _, grad, _ = orc.loss_and_gradient(prob.H0, prob.Hk, prob.c, prob.dt, V, "magnus4_gl2")
+    monkeypatch.undo()
+    entries = [(k, s) for k in range(2) for s in range(0, 10, 2)]
+    fd = _fd_gradient(prob, V, 1e-6, entries, "magnus4_gl2")
+    g = np.array([grad[k, s] for (k, s) in entries])
+    assert np.max(np.abs(g - fd)) > 1e-4 * np.max(np.abs(fd))
 
 
 def test_gradient_invariants():
