@@ -83,10 +83,14 @@ typedef enum {
  *  FP32: exponent assembly, exponential and the in-block tree in float; the
  *        norm bound that picks the Taylor degree and the number of squarings,
  *        and the product tree above the thread-block level, in double.
- *  FP32_TC_TF32X3: FP32 with the complex products of d >= 32 on the tensor
- *        cores: every FP32 operand split into two TF32 terms, three MMAs per
- *        real product (hi*hi + hi*lo + lo*hi), FP32 accumulation; FP64 norm
- *        bound and FP64 top tree as in FP32.  d < 32: PARAMENT_ERR_UNSUPPORTED.
+ *  FP32_TC_TF32X3: FP32 with the complex products of large d on the tensor
+ *        cores: every FP32 operand split into two round-to-nearest TF32 terms,
+ *        three MMAs per real product (hi*hi + hi*lo + lo*hi), FP32 accumulation
+ *        with a fresh accumulator per k-chunk; FP64 norm bound and FP64 top
+ *        tree as in FP32.  d in 65..128: tcgen05 with tensor-memory accumulators;
+ *        d in 129..256 (and the batched kernel's d = 128): mma.sync; d in 17..64:
+ *        the shared-memory CUDA-core product of FP32, which is faster there (and
+ *        at least as accurate).  d <= 16: PARAMENT_ERR_UNSUPPORTED.
  *  FP32_TC_BF16X3: not implemented in this build (PARAMENT_ERR_UNSUPPORTED).
  */
 typedef enum {
@@ -217,17 +221,20 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec);
 
 /*
  * Gate-fidelity loss and its gradient with respect to every control sample
- * (midpoint rule; Sec. 7 names GRAPE-type optimal control as the application,
- * the paper gives no gradient formula).  With z = Tr(V^dagger U(T)):
+ * (Sec. 7 names GRAPE-type optimal control as the application; the paper gives
+ * no gradient formula).  With z = Tr(V^dagger U(T)):
  *   *loss_out = 1 - |z|^2 / d^2                         (host double; NULL = skip, no wait)
- *   grad_out[k * N + j] = dL / dc_k(t_j)                (K x N; double for FP64, float for FP32)
- * U = S_j U_j P_{j-1}; dz/dc_kj = Tr(L_{X_j}(P_{j-1} V^dagger S_j) (-i dt H_k)) with X_j = -i G_j and
- * L_X the Frechet derivative of exp, taken as the upper-right block of exp([[X, Lambda], [0, X]]).
- * The prefixes P and suffixes S come from the forward tree: leaf and block products of the forward
- * kernel, exclusive scans over them, then per leaf a forward sweep (prefixes, re-computed from
- * checkpoints for long leaves) and a backward sweep.  V: d x d in the dtype of set_hamiltonians;
- * U_out: optional U(T).  Pointers host or device.  Errors: UNSUPPORTED for the Magnus integrators
- * and tensor-core precisions; STATE before set_controls.
+ *   grad_out[k * S + s] = dL / dc_k(sample s)           (K x S; double for FP64, float for FP32;
+ *                                                        S = N midpoint, 2N GL4, 2N + 1 Simpson)
+ * U = S_j U_j P_{j-1}; dz/dc = Tr(L_{X_j}(P_{j-1} V^dagger S_j) dX_j/dc) with X_j = -i G_j,
+ * dX_j/dc = -i sum_e (d gamma_e / dc) B_e over the effective-control basis (Sec. 4, Eq.
+ * magnus_coeffs: H0, H_k, i[H0, H_k], i[H_k, H_l]), and L_X the Frechet derivative of exp, taken
+ * as the upper-right block of exp([[X, Lambda], [0, X]]).  The prefixes P and suffixes S come from
+ * the forward tree: leaf and block products of the forward kernel, exclusive scans over them, then
+ * per leaf a forward sweep (prefixes, re-computed from checkpoints for long leaves) and a backward
+ * sweep.  A Simpson end sample belongs to two slices and receives both contributions.  V: d x d in
+ * the dtype of set_hamiltonians; U_out: optional U(T).  Pointers host or device.  d <= 16.
+ * Errors: UNSUPPORTED for d > 16 and the tensor-core precisions; STATE before set_controls.
  */
 int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, void *grad_out, void *U_out,
                             parament_precision prec);

@@ -1,8 +1,8 @@
 """torch.autograd wrapper of the adjoint gradient (parament_propagate_grad).
 
 ``gate_infidelity(prop, c, V, dt, prec)`` returns L = 1 - |Tr(V^dagger U(T))|^2 / d^2
-for the controls ``c`` (K, N) on a ``binding.Propagator`` whose Hamiltonians are
-set (midpoint rule).  The forward call runs the forward kernels and the adjoint
+for the control samples ``c`` (K, S) on a ``binding.Propagator`` whose Hamiltonians
+are set (any integrator; S as in set_controls).  The forward call runs the forward kernels and the adjoint
 kernels of the library at once; backward only scales the stored gradient.
 """
 

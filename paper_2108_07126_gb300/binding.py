@@ -383,11 +383,13 @@ class Propagator:
         return out
 
     def propagate_grad(self, V, prec: str = "fp64", want_U: bool = False):
-        """Loss 1 - |Tr(V^dagger U)|^2 / d^2, its gradient (K, N) w.r.t. the controls, optionally U."""
+        """Loss 1 - |Tr(V^dagger U)|^2 / d^2, its gradient (K, S) w.r.t. the control samples, optionally U."""
         torch = self._torch
         V = torch.as_tensor(V).to(self.dtype).to(self.device).contiguous()
         rdt = torch.float64 if prec == "fp64" else torch.float32
-        grad = torch.empty(self.n_ctrl, self.n_steps, dtype=rdt, device=self.device)
+        S = {"midpoint": self.n_steps, "magnus4_gl2": 2 * self.n_steps,
+             "magnus4_simpson": 2 * self.n_steps + 1}[self.integrator]
+        grad = torch.empty(self.n_ctrl, S, dtype=rdt, device=self.device)
         U = torch.empty(self.dim, self.dim, dtype=self.dtype, device=self.device) if want_U else None
         self._sync_stream()
         loss = parament_propagate_grad(self.ctx, V.data_ptr(), grad.data_ptr(), U.data_ptr() if want_U else None,

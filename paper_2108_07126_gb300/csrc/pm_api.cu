@@ -26,9 +26,9 @@ namespace pm {
     int fused_blocks_per_sm_d##D(int, int, int, size_t, int);                                            \
     size_t fused_smem_d##D(int, int, int);                                                               \
     int fused_groups_per_warp_d##D(int);                                                                 \
-    cudaError_t grad_run_d##D(int, const ScanParams &, const GradParams &, int, int, size_t, cudaStream_t); \
+    cudaError_t grad_run_d##D(int, int, const ScanParams &, const GradParams &, int, int, size_t, cudaStream_t); \
     cudaError_t scan_run_d##D(const ScanParams &, cudaStream_t);                                          \
-    int adjoint_blocks_per_sm_d##D(int, int, size_t);                                                     \
+    int adjoint_blocks_per_sm_d##D(int, int, int, size_t);                                                \
     size_t adjoint_smem_d##D(int, int, int);
 PM_DECL_D(2)
 PM_DECL_D(4)
@@ -546,13 +546,13 @@ size_t fused_smem(int Dp, int fp64, int nb, int warps) {
     }
     return 0;
 }
-cudaError_t grad_run(int Dp, int fp64, const ScanParams &sp, const GradParams &gp, int grid, int warps, size_t smem,
-                     cudaStream_t st) {
+cudaError_t grad_run(int Dp, int fp64, int integ, const ScanParams &sp, const GradParams &gp, int grid, int warps,
+                     size_t smem, cudaStream_t st) {
     switch (Dp) {
-        case 2: return grad_run_d2(fp64, sp, gp, grid, warps, smem, st);
-        case 4: return grad_run_d4(fp64, sp, gp, grid, warps, smem, st);
-        case 8: return grad_run_d8(fp64, sp, gp, grid, warps, smem, st);
-        case 16: return grad_run_d16(fp64, sp, gp, grid, warps, smem, st);
+        case 2: return grad_run_d2(fp64, integ, sp, gp, grid, warps, smem, st);
+        case 4: return grad_run_d4(fp64, integ, sp, gp, grid, warps, smem, st);
+        case 8: return grad_run_d8(fp64, integ, sp, gp, grid, warps, smem, st);
+        case 16: return grad_run_d16(fp64, integ, sp, gp, grid, warps, smem, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -565,12 +565,12 @@ cudaError_t scan_run(int Dp, const ScanParams &sp, cudaStream_t st) {
     }
     return cudaErrorInvalidValue;
 }
-int adjoint_blocks_per_sm(int Dp, int fp64, int warps, size_t smem) {
+int adjoint_blocks_per_sm(int Dp, int fp64, int integ, int warps, size_t smem) {
     switch (Dp) {
-        case 2: return adjoint_blocks_per_sm_d2(fp64, warps, smem);
-        case 4: return adjoint_blocks_per_sm_d4(fp64, warps, smem);
-        case 8: return adjoint_blocks_per_sm_d8(fp64, warps, smem);
-        case 16: return adjoint_blocks_per_sm_d16(fp64, warps, smem);
+        case 2: return adjoint_blocks_per_sm_d2(fp64, integ, warps, smem);
+        case 4: return adjoint_blocks_per_sm_d4(fp64, integ, warps, smem);
+        case 8: return adjoint_blocks_per_sm_d8(fp64, integ, warps, smem);
+        case 16: return adjoint_blocks_per_sm_d16(fp64, integ, warps, smem);
     }
     return 0;
 }
@@ -1119,8 +1119,6 @@ int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, 
     ctx->err.clear();
     if (ctx->state < 2) return set_err(ctx, PARAMENT_ERR_STATE, "set_hamiltonians and set_controls must come first");
     if (!V || !grad_out) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "null V or grad_out");
-    if (ctx->integ != PARAMENT_MIDPOINT)
-        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "the adjoint gradient covers the midpoint rule");
     if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32)
         return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "gradient precision must be FP64 or FP32");
     if (ctx->dpad > kMaxSmallDim)
@@ -1172,7 +1170,7 @@ int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, 
     while (aw > 1 && adjoint_smem(Dp, fp64, K, aw) > ctx->smem_optin) --aw;
     const size_t asmem = adjoint_smem(Dp, fp64, K, aw);
     if (asmem > ctx->smem_optin) return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "adjoint needs %zu B shared memory", asmem);
-    const int abps = adjoint_blocks_per_sm(Dp, fp64, aw, asmem);
+    const int abps = adjoint_blocks_per_sm(Dp, fp64, (int)ctx->integ, aw, asmem);
     if (abps <= 0) return set_err(ctx, PARAMENT_ERR_CUDA, "adjoint occupancy query failed");
     const int agrid = abps * ctx->sm_count;
     const int64_t TG = (int64_t)agrid * aw * fused_gpw(Dp, fp64);
@@ -1187,7 +1185,7 @@ int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, 
 
     void *gdst = grad_out;
     const bool host_g = !is_device_ptr(grad_out);
-    const size_t gbytes = (size_t)K * N * rsz;
+    const size_t gbytes = (size_t)K * ctx->S * rsz;
     if (host_g) {
         if ((st = ws_reserve(ctx, ctx->ggrad, std::max<size_t>(gbytes, 8)))) return st;
         gdst = ctx->ggrad.ptr;
@@ -1211,14 +1209,15 @@ int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, 
     GradParams gp;
     std::memset(&gp, 0, sizeof(gp));
     gp.ctrl = p.ctrl;
+    gp.S = ctx->S;
     gp.n_steps = N;
     gp.K = K;
     gp.n_basis = ctx->nb_eff;
+    gp.n_coef = ctx->nb;
     gp.dt = ctx->dt;
     for (int e = 0; e < kMaxBasis; ++e) gp.slot_of[e] = ctx->slot_of[e];
     gp.packed = p.packed;
     gp.bnorm1 = p.bnorm1;
-    gp.hk = (const double2 *)ctx->full.ptr + DD;  // basis entries 1..K are the H_k
     gp.pin = sp.pin;
     gp.sout = sp.sout;
     gp.vdag = sp.vdag;
@@ -1247,7 +1246,8 @@ int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, 
         std::memcpy(gp.dcls_cap, tmp.cls_cap, sizeof(gp.dcls_cap));
         std::memcpy(gp.dcls_code, tmp.cls_code, sizeof(gp.dcls_code));
     }
-    PM_CUDA(grad_run(Dp, fp64, sp, gp, agrid, aw, asmem, ctx->stream));
+    if (gbytes) PM_CUDA(cudaMemsetAsync(gdst, 0, gbytes, ctx->stream));  // Simpson end points accumulate
+    PM_CUDA(grad_run(Dp, fp64, (int)ctx->integ, sp, gp, agrid, aw, asmem, ctx->stream));
     ctx->last.grad_subchunk = (int32_t)c_sub;
 
     if (host_g && gbytes) PM_CUDA(cudaMemcpyAsync(grad_out, gdst, gbytes, cudaMemcpyDeviceToHost, ctx->stream));

@@ -119,11 +119,11 @@ __global__ void __launch_bounds__(256, 1) batched_kernel(const BatchItem *__rest
             case 8: fused_body<Real, 8, INTEG>(p, w.blk, w.nblk, smem); break;
             case 16: fused_body<Real, 16, INTEG>(p, w.blk, w.nblk, smem); break;
             case 32:
-                large_body<Real, 32, INTEG, TC ? 1 : 0>(p, (C *)ws, w.blk, w.nblk, smem);
+                large_body<Real, 32, INTEG, 0>(p, (C *)ws, w.blk, w.nblk, smem);  // faster than 3xTF32 here
                 large_arrival_tree<32>(p, ws, w.blk, w.nblk, smem);
                 break;
             case 64:
-                large_body<Real, 64, INTEG, TC ? 1 : 0>(p, (C *)ws, w.blk, w.nblk, smem);
+                large_body<Real, 64, INTEG, 0>(p, (C *)ws, w.blk, w.nblk, smem);  // faster than 3xTF32 here
                 large_arrival_tree<64>(p, ws, w.blk, w.nblk, smem);
                 break;
             case 128:

@@ -187,8 +187,9 @@ template <> __device__ __forceinline__ double pow2neg<double>(int s) {
 
 // Effective coefficients gamma_e of one slice (Sec. 4, Eq. magnus_coeffs with the
 // commutator sign of Omega_2): basis order H0, H_k, i[H0,H_k], i[H_k,H_k'] (k < k').
-template <typename Real, int INTEG, int STRIDE = 32>
-__device__ __forceinline__ void slice_coefficients(const FusedParams &p, int64_t j, bool active, Real *gam) {
+// P: any parameter block with ctrl, S, K, dt, n_basis and slot_of (FusedParams, GradParams).
+template <typename Real, int INTEG, int STRIDE = 32, typename P = FusedParams>
+__device__ __forceinline__ void slice_coefficients(const P &p, int64_t j, bool active, Real *gam) {
     const Real *c = (const Real *)p.ctrl;
     const int K = p.K;
     const Real h = (Real)p.dt;

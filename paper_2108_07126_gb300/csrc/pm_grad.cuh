@@ -1,11 +1,11 @@
 // Adjoint gradient of the gate-fidelity loss L = 1 - |Tr(V^dagger U)|^2 / d^2
-// with respect to every control sample c_k(t_j) (midpoint rule).
+// with respect to every control sample (all three integrators).
 //
 // U = S_j U_j P_{j-1} with the exclusive prefix P_{j-1} = U_{j-1} ... U_1 and
 // suffix S_j = U_N ... U_{j+1}; with z = Tr(V^dagger U) and X_j = -i G_j,
-//   dz/dc_kj = Tr(Lambda_j L_{X_j}(E_k)) = Tr(L_{X_j}(Lambda_j) E_k),
-//   Lambda_j = P_{j-1} V^dagger S_j,  E_k = -i dt H_k,
-//   dL/dc_kj = -(2/d^2) Re(conj(z) dz/dc_kj),
+//   dz/dc = Tr(Lambda_j L_{X_j}(dX_j/dc)) = Tr(L_{X_j}(Lambda_j) dX_j/dc),
+//   Lambda_j = P_{j-1} V^dagger S_j,  dX_j/dc = -i sum_e (d gamma_e / dc) B_e,
+//   dL/dc = -(2/d^2) Re(conj(z) dz/dc),
 // where L_X(E) is the Frechet derivative of exp at X (L_X is self-adjoint under
 // the trace pairing).  M_j = L_{X_j}(Lambda_j) is the upper-right block of
 // exp([[X_j, Lambda_j], [0, X_j]]) (Van Loan), evaluated with the same Taylor /
@@ -28,20 +28,21 @@
 namespace pm {
 
 struct GradParams {
-    const void *ctrl;        // Real [K][N] (midpoint samples)
+    const void *ctrl;        // Real [K][S] control samples
+    int64_t S;               // samples per control (N, 2N or 2N + 1)
     int64_t n_steps;
     int K;
-    int n_basis;
+    int n_basis;             // kept basis matrices
+    int n_coef;              // effective coefficients per slice (kept or not)
     double dt;
     short slot_of[kMaxBasis];
     const void *packed;      // Real [n_basis][D][D] packed basis (kept matrices)
     const double *bnorm1;    // [n_basis]
-    const double2 *hk;       // [K][D][D] control Hamiltonians (FP64, padded)
     const double2 *pin;      // [L][D][D] exclusive prefix of each leaf
     const double2 *sout;     // [L][D][D] exclusive suffix of each leaf
     const double2 *vdag;     // [D][D] V^dagger (padded with zeros)
     const double *z;         // z = Tr(V^dagger U): z[0] + i z[1]
-    void *grad;              // Real [K][N]
+    void *grad;              // Real [K][S], zeroed before the launch (Simpson end points add up)
     void *pbuf;              // Real complex [groups][c_sub][D][D]: prefixes of one sub-chunk
     void *ckpt;              // Real complex [groups][n_ckpt][D][D]: sub-chunk checkpoints
     int c_sub, n_ckpt;
@@ -171,26 +172,31 @@ __global__ void __launch_bounds__(256) scan_leaves_kernel(const ScanParams sp) {
 
 // ---------------------------------------------------------------- the adjoint kernel
 
+// per group: 10 complex D x LD slots, then the traces Tr(M B_e) of one slice (kMaxBasis complex,
+// rounded up to 16 bytes: the slots of the next group take 16-byte vector accesses)
 template <typename Real, int D>
-__host__ __device__ inline size_t adjoint_group_bytes() {
+__host__ __device__ constexpr size_t adjoint_group_bytes() {
     using G = Geo<Real, D>;
-    return (size_t)10 * G::SLOT * sizeof(typename G::C) + Tiling<Real, D>::GPAD;
+    return (size_t)10 * G::SLOT * sizeof(typename G::C) +
+           (((size_t)kMaxBasis * sizeof(typename G::C) + 15) & ~(size_t)15) + Tiling<Real, D>::GPAD;
 }
 
 template <typename Real, int D>
 __host__ __device__ inline size_t adjoint_smem_bytes(int K, int warps) {
     using G = Geo<Real, D>;
-    const size_t hk = ((size_t)K * D * D * sizeof(typename G::C) + 15) & ~(size_t)15;
-    return hk + (size_t)warps * G::GPW * adjoint_group_bytes<Real, D>();
+    (void)K;
+    return (size_t)warps * G::GPW * adjoint_group_bytes<Real, D>();
 }
 
 template <typename Real> __device__ __forceinline__ Real gcoef(const GradParams &p, int k);
 template <> __device__ __forceinline__ float gcoef<float>(const GradParams &p, int k) { return p.coef_f[k]; }
 template <> __device__ __forceinline__ double gcoef<double>(const GradParams &p, int k) { return p.coef_d[k]; }
 
-template <typename Real, int D>
+template <typename Real, int D, int INTEG>
 __global__ void __launch_bounds__(256, 1) adjoint_kernel(const GradParams p) {
     using G = Geo<Real, D>;
+    static_assert(adjoint_group_bytes<Real, D>() % 16 == 0 && (G::SLOT * sizeof(typename G::C)) % 16 == 0,
+                  "group workspaces and slots must stay 16-byte aligned");
     using C = typename G::C;
     constexpr int LANES = G::LANES, GPW = G::GPW, TR = G::TR, TC = G::TC, LD = G::LD, DD = G::DD;
     constexpr int SLOT = G::SLOT, NCH = G::NCH, PS = G::PS;
@@ -201,18 +207,11 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const GradParams p) {
     const int rb = gl / G::CBW, cb = gl % G::CBW;
     const int K = p.K, nb = p.n_basis;
 
-    C *hk = (C *)smem;
-    const size_t hk_bytes = ((size_t)K * DD * sizeof(C) + 15) & ~(size_t)15;
-    C *slots = (C *)(smem + hk_bytes + (size_t)(warp * GPW + g) * adjoint_group_bytes<Real, D>());
+    C *slots = (C *)(smem + (size_t)(warp * GPW + g) * adjoint_group_bytes<Real, D>());
     C *SX = slots, *SX2 = slots + SLOT, *SX3 = slots + 2 * SLOT;
     C *SD1 = slots + 3 * SLOT, *SD2 = slots + 4 * SLOT, *SD3 = slots + 5 * SLOT;
     C *STL = slots + 6 * SLOT, *STR = slots + 7 * SLOT, *SW = slots + 8 * SLOT, *SP = slots + 9 * SLOT;
-
-    for (int e = tid; e < K * DD; e += blockDim.x) {
-        const double2 v = p.hk[e];
-        hk[e] = Cx<Real>::make((Real)v.x, (Real)v.y);
-    }
-    __syncthreads();
+    C *Ttr = slots + 10 * SLOT;  // Tr(M B_e) of the kept basis matrices
 
     const Real *ctrl = (const Real *)p.ctrl;
     const Real *packed = (const Real *)p.packed;
@@ -223,7 +222,7 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const GradParams p) {
     C *pbuf = (C *)p.pbuf + (size_t)gid * p.c_sub * DD;
     C *ckpt = (C *)p.ckpt + (size_t)gid * p.n_ckpt * DD;
     const Real zr = (Real)p.z[0], zi = (Real)p.z[1];
-    const Real gscale = (Real)(-2.0 * p.dt / (p.d_true * p.d_true));
+    const Real gscale = (Real)(-2.0 / (p.d_true * p.d_true));
     unsigned flags = 0;
 
     // lane tile helpers
@@ -258,15 +257,9 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const GradParams p) {
 
     // Exponent of slice j into SX as A = -i G_j / 2^s; returns the class (warp-uniform)
     auto prep = [&](int64_t j, bool active, bool deriv) -> int {
-        Real gam[1 + kMaxControls];
+        Real gam[kMaxBasis];
         for (int e = 0; e < nb; ++e) gam[e] = Real(0);
-        if (active) {
-            if (p.slot_of[0] >= 0) gam[p.slot_of[0]] = h;
-            for (int k = 0; k < K; ++k) {
-                const int sl = p.slot_of[1 + k];
-                if (sl >= 0) gam[sl] = h * ctrl[(int64_t)k * N + j];
-            }
-        }
+        slice_coefficients<Real, INTEG, 1>(p, j, active, gam);
         double nu = 0.0;
         for (int e = 0; e < nb; ++e) nu = fma(fabs((double)gam[e]), p.bnorm1[e], nu);
         int c;
@@ -509,25 +502,81 @@ __global__ void __launch_bounds__(256, 1) adjoint_kernel(const GradParams p) {
                     __syncwarp();
                 }
                 block_exp(code, true, U, M);
-                // dL/dc_kj = -(2/d^2) dt (Re z Im T_k - Im z Re T_k),  T_k = Tr(M H_k)
-                for (int k = 0; k < K; ++k) {
+                // T_e = Tr(M B_e) for every kept basis matrix, from its packed real form
+                // (upper triangle: Re, strict lower: Im); element (i, jj) of M meets B_e[jj][i]
+                for (int e = 0; e < nb; ++e) {
+                    const Real *Pe = packed + (size_t)e * DD;
                     Real tr = 0, ti = 0;
 #pragma unroll
                     for (int r = 0; r < TR; ++r)
 #pragma unroll
                         for (int c = 0; c < TC; ++c) {
                             const int i = rb + r * G::RBN, jj = G::col(cb, c);
-                            const C hv = hk[(size_t)k * DD + jj * D + i];
-                            tr = fma(M[r][c].x, hv.x, fma(-M[r][c].y, hv.y, tr));
-                            ti = fma(M[r][c].x, hv.y, fma(M[r][c].y, hv.x, ti));
+                            const Real a = __ldg(Pe + jj * D + i), b = __ldg(Pe + i * D + jj);
+                            const Real br = (jj <= i) ? a : b;
+                            const Real bi = (jj > i) ? a : ((jj < i) ? -b : Real(0));
+                            tr = fma(M[r][c].x, br, fma(-M[r][c].y, bi, tr));
+                            ti = fma(M[r][c].x, bi, fma(M[r][c].y, br, ti));
                         }
 #pragma unroll
                     for (int off = LANES / 2; off > 0; off >>= 1) {
                         tr += __shfl_xor_sync(0xffffffffu, tr, off);
                         ti += __shfl_xor_sync(0xffffffffu, ti, off);
                     }
-                    if (gl == 0 && act) ((Real *)p.grad)[(size_t)k * N + j] = gscale * (zr * ti - zi * tr);
+                    if (gl == 0) Ttr[e] = Cx<Real>::make(tr, ti);
                 }
+                __syncwarp();
+                // dL/dc = -(2/d^2) (Re z Im Q - Im z Re Q),  Q = sum_e (d gamma_e / dc) T_e
+                if (act) {
+                    auto T = [&](int raw) -> C {
+                        const int sl = p.slot_of[raw];
+                        return sl >= 0 ? Ttr[sl] : Cx<Real>::make(Real(0), Real(0));
+                    };
+                    auto emit = [&](int k, int64_t sidx, C q) {
+                        Real *gr = (Real *)p.grad + (size_t)k * p.S + sidx;
+                        const Real v = gscale * (zr * q.y - zi * q.x);
+                        if (INTEG == kSimpson) atomicAdd(gr, v);  // end points are shared by two slices
+                        else *gr = v;
+                    };
+                    auto axpy = [](C &q, Real a, C t) {
+                        q.x = fma(a, t.x, q.x);
+                        q.y = fma(a, t.y, q.y);
+                    };
+                    const int R = (INTEG == kMidpoint) ? 1 : ((INTEG == kGL2) ? 2 : 3);
+                    for (int w = gl; w < K * R; w += LANES) {
+                        const int k = w / R, role = w % R;
+                        C q = Cx<Real>::make(Real(0), Real(0));
+                        if (INTEG == kMidpoint) {
+                            axpy(q, h, T(1 + k));
+                            emit(k, j, q);
+                        } else {
+                            // samples of the slice: GL4 nodes (2j, 2j + 1); Simpson (2j, 2j + 1, 2j + 2)
+                            const Real wc = (INTEG == kGL2) ? (Real)(1.7320508075688772 / 12.0) * h * h : h * h / Real(12);
+                            const Real w1 = (INTEG == kGL2) ? h * Real(0.5) : h / Real(6);
+                            const int64_t s1 = 2 * j, s2 = (INTEG == kGL2) ? 2 * j + 1 : 2 * j + 2;
+                            if (INTEG == kSimpson && role == 1) {  // centre sample: Omega_1 only
+                                axpy(q, Real(4) * h / Real(6), T(1 + k));
+                                emit(k, 2 * j + 1, q);
+                                continue;
+                            }
+                            const bool first = (role == 0);  // c1 (first node / start) or c2 (second node / end)
+                            axpy(q, w1, T(1 + k));
+                            axpy(q, first ? -wc : wc, T(1 + K + k));
+                            // pairs (a, b), a < b: gamma = wc (c1_a c2_b - c2_a c1_b)
+                            int e = 1 + 2 * K;
+                            for (int a = 0; a < K; ++a)
+                                for (int b = a + 1; b < K; ++b, ++e) {
+                                    if (a != k && b != k) continue;
+                                    Real coef;
+                                    if (first) coef = (k == a) ? wc * ctrl[(int64_t)b * p.S + s2] : -wc * ctrl[(int64_t)a * p.S + s2];
+                                    else coef = (k == b) ? wc * ctrl[(int64_t)a * p.S + s1] : -wc * ctrl[(int64_t)b * p.S + s1];
+                                    axpy(q, coef, T(e));
+                                }
+                            emit(k, first ? s1 : s2, q);
+                        }
+                    }
+                }
+                __syncwarp();
                 // W <- W U_j
                 st_tile<Real, D>(STL, rb, cb, U);
                 __syncwarp();

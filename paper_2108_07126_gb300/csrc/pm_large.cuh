@@ -551,10 +551,12 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
     __syncthreads();
 }
 
-// products of the standalone large kernel: tcgen05 for FP32 D = 128, mma.sync for smaller D
+// products of the 3xTF32 precision in the standalone large kernel: tcgen05 for D = 128, mma.sync
+// for D = 256; at D <= 64 the shared-memory CUDA-core product is faster than both (and at least as
+// accurate) and is used instead
 template <typename Real, int D, bool TC>
 __host__ __device__ constexpr int large_tcm() {
-    return !TC ? 0 : ((D == 128 && std::is_same<Real, float>::value) ? 2 : 1);
+    return (!TC || !std::is_same<Real, float>::value || D <= 64) ? 0 : (D == 128 ? 2 : 1);
 }
 
 template <typename Real, int D, int INTEG, bool TC = false>

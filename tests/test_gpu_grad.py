@@ -1,4 +1,5 @@
-"""Adjoint gradient on the GPU against the oracle's Daleckii-Krein gradient and finite differences.
+"""Adjoint gradient on the GPU against the oracle's Daleckii-Krein gradient and finite differences
+(midpoint rule and both fourth-order Magnus integrators).
 
 FP64: the adjoint gradient agrees with the oracle to 1e-9 relative to max |g|
 (the two use different exponential and Frechet-derivative algorithms; the bound
@@ -31,7 +32,7 @@ def prop():
     p.close()
 
 
-def gpu_grad(prop, prob, V, prec="fp64", subchunk=0):
+def gpu_grad(prop, prob, V, prec="fp64", subchunk=0, integrator="midpoint"):
     import torch
 
     from paper_2108_07126_gb300 import binding as b
@@ -39,7 +40,7 @@ def gpu_grad(prop, prob, V, prec="fp64", subchunk=0):
     cdt = torch.complex128 if prec == "fp64" else torch.complex64
     rdt = torch.float64 if prec == "fp64" else torch.float32
     prop.set_option(b.PARAMENT_OPT_GRAD_SUBCHUNK, subchunk)
-    prop.set_hamiltonians(torch.as_tensor(prob.H0).to(cdt), torch.as_tensor(prob.Hk).to(cdt), "midpoint")
+    prop.set_hamiltonians(torch.as_tensor(prob.H0).to(cdt), torch.as_tensor(prob.Hk).to(cdt), integrator)
     prop.set_controls(torch.as_tensor(prob.c).to(rdt), prob.dt, prob.n_steps)
     loss, grad, U = prop.propagate_grad(torch.as_tensor(V).to(cdt), prec, want_U=True)
     torch.cuda.synchronize()
@@ -127,16 +128,53 @@ def test_gradient_invariants(prop):
     assert abs(loss_u) <= 1e-12 and np.max(np.abs(grad_u)) <= 1e-10
 
 
+@pytest.mark.parametrize("integrator", ["magnus4_gl2", "magnus4_simpson"])
+@pytest.mark.parametrize("d,K,N", [(2, 1, 1), (2, 2, 9), (3, 3, 200), (4, 2, 129), (8, 4, 300), (16, 3, 65),
+                                   (5, 5, 31)])
+def test_fp64_magnus_gradient_matches_oracle(prop, integrator, d, K, N):
+    """Magnus integrators: every sample's derivative through the effective-control basis
+    (commutator terms included; Simpson end samples get the contributions of both slices)."""
+    prob = wl.random_problem(d, K, N, integrator, seed=540 + d * 10 + K, g_norm=0.4)
+    V = wl.haar_unitary(np.random.default_rng(d + N + 1), d)
+    loss, grad, U = gpu_grad(prop, prob, V, integrator=integrator)
+    l_ref, g_ref, U_ref = oracle.loss_and_gradient(prob.H0, prob.Hk, prob.c, prob.dt, V, integrator)
+    assert grad.shape == g_ref.shape == prob.c.shape
+    assert abs(loss - l_ref) <= 1e-11
+    assert np.max(np.abs(U - U_ref)) <= 1e-11
+    assert np.max(np.abs(grad - g_ref)) <= 1e-9 * np.max(np.abs(g_ref))
+
+
+@pytest.mark.parametrize("integrator", ["magnus4_gl2", "magnus4_simpson"])
+def test_fp32_magnus_gradient_error(prop, integrator):
+    prob = wl.random_problem(8, 3, 2000, integrator, seed=560, g_norm=0.3)
+    V = wl.haar_unitary(np.random.default_rng(561), 8)
+    loss, grad, _ = gpu_grad(prop, prob, V, "fp32", integrator=integrator)
+    l_ref, g_ref, _ = oracle.loss_and_gradient(prob.H0, prob.Hk, prob.c, prob.dt, V, integrator)
+    rel = np.max(np.abs(grad - g_ref)) / np.max(np.abs(g_ref))
+    assert rel <= 3e-3, rel
+
+
+def test_magnus_gradient_checkpoints_agree(prop):
+    prob = wl.random_problem(4, 2, 700, "magnus4_simpson", seed=570, g_norm=0.3)
+    V = wl.haar_unitary(np.random.default_rng(571), 4)
+    _, g_full, _ = gpu_grad(prop, prob, V, integrator="magnus4_simpson")
+    _, g_ck, _ = gpu_grad(prop, prob, V, subchunk=5, integrator="magnus4_simpson")
+    assert np.max(np.abs(g_ck - g_full)) <= 1e-12 * np.max(np.abs(g_full))
+
+
 def test_gradient_errors(prop):
     import torch
 
     from paper_2108_07126_gb300 import binding as b
 
-    prob = wl.random_problem(4, 2, 10, "magnus4_gl2", seed=1)
-    prop.set_hamiltonians(torch.as_tensor(prob.H0), torch.as_tensor(prob.Hk), "magnus4_gl2")
+    prob = wl.random_problem(32, 1, 10, "midpoint", seed=1)
+    prop.set_hamiltonians(torch.as_tensor(prob.H0), torch.as_tensor(prob.Hk), "midpoint")
     prop.set_controls(torch.as_tensor(prob.c), prob.dt, 10)
     with pytest.raises(b.ParamentError) as e:
-        prop.propagate_grad(np.eye(4))
+        prop.propagate_grad(np.eye(32))
+    assert e.value.status == b.PARAMENT_ERR_UNSUPPORTED
+    with pytest.raises(b.ParamentError) as e:
+        prop.propagate_grad(np.eye(32), "fp32_tc_tf32x3")
     assert e.value.status == b.PARAMENT_ERR_UNSUPPORTED
 
 
