@@ -107,7 +107,8 @@ typedef enum {
     PARAMENT_OPT_TAYLOR_DEGREE = 1,
     /* thread blocks of the fused kernel; 0 (default) = fill every SM */
     PARAMENT_OPT_GRID_BLOCKS = 2,
-    /* warps per thread block; 0 (default) = largest that fits shared memory, capped at 8 */
+    /* warps per thread block; 0 (default) = largest that fits shared memory (at most 16 for FP32
+       d in 9..16, 8 otherwise) */
     PARAMENT_OPT_BLOCK_WARPS = 3,
     /* 1 (default) = reject non-Hermitian H in set_hamiltonians; 0 = skip the check */
     PARAMENT_OPT_CHECK_HERMITIAN = 4,

@@ -26,6 +26,7 @@ namespace pm {
     int fused_blocks_per_sm_d##D(int, int, int, size_t, int);                                            \
     size_t fused_smem_d##D(int, int, int);                                                               \
     int fused_groups_per_warp_d##D(int);                                                                 \
+    int fused_max_warps_d##D(int);                                                                       \
     cudaError_t grad_run_d##D(int, int, const ScanParams &, const GradParams &, int, int, size_t, cudaStream_t); \
     cudaError_t scan_run_d##D(const ScanParams &, cudaStream_t);                                          \
     int adjoint_blocks_per_sm_d##D(int, int, int, size_t);                                                \
@@ -615,6 +616,15 @@ size_t large_smem(int Dp, int fp64, int nb, int tc = 0) {
     }
     return 0;
 }
+int fused_max_warps(int Dp, int fp64) {
+    switch (Dp) {
+        case 2: return fused_max_warps_d2(fp64);
+        case 4: return fused_max_warps_d4(fp64);
+        case 8: return fused_max_warps_d8(fp64);
+        case 16: return fused_max_warps_d16(fp64);
+    }
+    return 8;
+}
 int fused_gpw(int Dp, int fp64) {
     switch (Dp) {
         case 2: return fused_groups_per_warp_d2(fp64);
@@ -950,12 +960,13 @@ int forward_setup(parament_ctx *ctx, int fp64, void *U_dst, FusedParams &p, int 
         int st = ws_reserve(ctx, ctx->lscratch, (size_t)grid * 6 * Dp * Dp * csz);
         if (st) return st;
     } else {
+    const int max_warps = fused_max_warps(Dp, fp64);
     warps = (int)ctx->opt_warps;
     if (warps <= 0) {
-        warps = 8;
+        warps = max_warps;
         while (warps > 1 && fused_smem(Dp, fp64, nb, warps) > ctx->smem_optin) --warps;
     }
-    if (warps > 8) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "at most 8 warps per block");
+    if (warps > max_warps) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "at most %d warps per block", max_warps);
     smem = fused_smem(Dp, fp64, nb, warps);
     if (smem > ctx->smem_optin)
         return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "basis of %d matrices (d=%d) needs %zu B shared memory > %zu",
@@ -1396,7 +1407,7 @@ int parament_set_option(parament_ctx *ctx, int key, int64_t value) {
             ctx->opt_grid = value;
             return PARAMENT_OK;
         case PARAMENT_OPT_BLOCK_WARPS:
-            if (value < 0 || value > 8) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "block warps must be in [0, 8]");
+            if (value < 0 || value > 16) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "block warps must be in [0, 16]");
             ctx->opt_warps = value;
             return PARAMENT_OK;
         case PARAMENT_OPT_CHECK_HERMITIAN:

@@ -29,19 +29,21 @@ namespace pm {
 // Lane (rb, cb) owns rows rb + r * RBN (r < TR) and columns col(cb, c) (c < TC);
 // V complex numbers move per shared-memory access (V = 2: 16-byte float4).
 template <typename Real, int D> struct Tiling;
-template <> struct Tiling<float, 16> { static constexpr int LANES = 16, TR = 4, TC = 4, LD = 20, V = 2, GPAD = 16; };
-template <> struct Tiling<float, 8> { static constexpr int LANES = 4, TR = 4, TC = 4, LD = 8, V = 2, GPAD = 16; };
-template <> struct Tiling<float, 4> { static constexpr int LANES = 1, TR = 4, TC = 4, LD = 4, V = 2, GPAD = 16; };
-template <> struct Tiling<float, 2> { static constexpr int LANES = 1, TR = 2, TC = 2, LD = 2, V = 2, GPAD = 16; };
-template <> struct Tiling<double, 16> { static constexpr int LANES = 32, TR = 2, TC = 4, LD = 17, V = 1, GPAD = 0; };
-template <> struct Tiling<double, 8> { static constexpr int LANES = 8, TR = 2, TC = 4, LD = 9, V = 1, GPAD = 16; };
-template <> struct Tiling<double, 4> { static constexpr int LANES = 2, TR = 2, TC = 4, LD = 4, V = 1, GPAD = 16; };
-template <> struct Tiling<double, 2> { static constexpr int LANES = 1, TR = 2, TC = 2, LD = 2, V = 1, GPAD = 16; };
+// MAXW: most warps of a standalone fused block (its launch bound; the host picks fewer when the
+// shared memory does not fit them).
+template <> struct Tiling<float, 16> { static constexpr int LANES = 32, TR = 4, TC = 2, LD = 20, V = 2, GPAD = 16, MAXW = 16; };
+template <> struct Tiling<float, 8> { static constexpr int LANES = 4, TR = 4, TC = 4, LD = 8, V = 2, GPAD = 16, MAXW = 8; };
+template <> struct Tiling<float, 4> { static constexpr int LANES = 1, TR = 4, TC = 4, LD = 4, V = 2, GPAD = 16, MAXW = 8; };
+template <> struct Tiling<float, 2> { static constexpr int LANES = 1, TR = 2, TC = 2, LD = 2, V = 2, GPAD = 16, MAXW = 8; };
+template <> struct Tiling<double, 16> { static constexpr int LANES = 32, TR = 2, TC = 4, LD = 17, V = 1, GPAD = 0, MAXW = 8; };
+template <> struct Tiling<double, 8> { static constexpr int LANES = 8, TR = 2, TC = 4, LD = 9, V = 1, GPAD = 16, MAXW = 8; };
+template <> struct Tiling<double, 4> { static constexpr int LANES = 2, TR = 2, TC = 4, LD = 4, V = 1, GPAD = 16, MAXW = 8; };
+template <> struct Tiling<double, 2> { static constexpr int LANES = 1, TR = 2, TC = 2, LD = 2, V = 1, GPAD = 16, MAXW = 8; };
 
 template <typename Real, int D> struct Geo {
     using T = Tiling<Real, D>;
     using C = typename Cx<Real>::T;
-    static constexpr int LANES = T::LANES, TR = T::TR, TC = T::TC, LD = T::LD, V = T::V;
+    static constexpr int LANES = T::LANES, TR = T::TR, TC = T::TC, LD = T::LD, V = T::V, MAXW = T::MAXW;
     static constexpr int GPW = 32 / LANES;        // groups per warp
     static constexpr int RBN = D / TR;            // row blocks: rows rb + r * RBN
     static constexpr int CBW = D / TC;            // column blocks
@@ -756,7 +758,7 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
 }
 
 template <typename Real, int D, int INTEG, int EXPM = 0>
-__global__ void __launch_bounds__(256, 1) fused_small_kernel(const FusedParams p) {
+__global__ void __launch_bounds__(Geo<Real, D>::MAXW * 32, 1) fused_small_kernel(const FusedParams p) {
     extern __shared__ __align__(16) unsigned char smem[];
     fused_body<Real, D, INTEG, EXPM>(p, blockIdx.x, gridDim.x, smem);
 }

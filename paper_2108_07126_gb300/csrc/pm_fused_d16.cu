@@ -59,4 +59,6 @@ size_t fused_smem_d16(int fp64, int n_basis, int warps) {
 
 int fused_groups_per_warp_d16(int fp64) { return fp64 ? Geo<double, 16>::GPW : Geo<float, 16>::GPW; }
 
+int fused_max_warps_d16(int fp64) { return fp64 ? Geo<double, 16>::MAXW : Geo<float, 16>::MAXW; }
+
 }  // namespace pm

@@ -59,4 +59,6 @@ size_t fused_smem_d2(int fp64, int n_basis, int warps) {
 
 int fused_groups_per_warp_d2(int fp64) { return fp64 ? Geo<double, 2>::GPW : Geo<float, 2>::GPW; }
 
+int fused_max_warps_d2(int fp64) { return fp64 ? Geo<double, 2>::MAXW : Geo<float, 2>::MAXW; }
+
 }  // namespace pm

@@ -59,4 +59,6 @@ size_t fused_smem_d4(int fp64, int n_basis, int warps) {
 
 int fused_groups_per_warp_d4(int fp64) { return fp64 ? Geo<double, 4>::GPW : Geo<float, 4>::GPW; }
 
+int fused_max_warps_d4(int fp64) { return fp64 ? Geo<double, 4>::MAXW : Geo<float, 4>::MAXW; }
+
 }  // namespace pm

@@ -59,4 +59,6 @@ size_t fused_smem_d8(int fp64, int n_basis, int warps) {
 
 int fused_groups_per_warp_d8(int fp64) { return fp64 ? Geo<double, 8>::GPW : Geo<float, 8>::GPW; }
 
+int fused_max_warps_d8(int fp64) { return fp64 ? Geo<double, 8>::MAXW : Geo<float, 8>::MAXW; }
+
 }  // namespace pm
