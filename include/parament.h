@@ -130,7 +130,8 @@ typedef enum {
     /* exponential of parament_propagate: 0 (default) = Taylor with scaling and squaring, degree per
        slice; 1 = the paper's Chebyshev series (Sec. 2.1, Algorithm 1) with one spectral interval
        [-beta, beta] for all slices (beta = largest per-slice norm bound, found on the device) and the
-       degree of Eq. error_chebychev; d <= 16 */
+       degree of Eq. error_chebychev; every d and precision.  Trajectories reject it
+       (PARAMENT_ERR_UNSUPPORTED); the gradient always uses the Taylor exponential */
     PARAMENT_OPT_EXP_METHOD = 13,
     /* FP32 and tensor-core precisions: 1 (default) = one Newton-Schulz step R <- R (3 I - R^dagger R) / 2
        on every leaf product (the exact product is unitary; FP32 rounding that repeats from slice to

@@ -1078,8 +1078,6 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) 
     int grid = 0, warps = 0, lpb = 0;
     size_t smem = 0;
     const int cheb = ctx->opt_exp_method == 1;
-    if (cheb && ctx->dpad > kMaxSmallDim)
-        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "the Chebyshev exponential is built for d <= %d", kMaxSmallDim);
     int st = forward_setup(ctx, fp64, dst, p, grid, warps, smem, lpb, tc);
     if (st) return st;
     if (cheb) {
@@ -1109,9 +1107,14 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) 
         p.cheb_m = mptr;
         p.cheb_inv_beta = ibeta;
         p.cheb_coef = coef;
-        if (fused_blocks_per_sm(ctx->dpad, fp64, ig, warps, smem, 1) <= 0)
-            return set_err(ctx, PARAMENT_ERR_CUDA, "occupancy query failed (Chebyshev kernel)");
-        PM_CUDA(fused_dispatch(ctx->dpad, fp64, ig, p, grid, warps, smem, ctx->stream, 1));
+        if (ctx->dpad > kMaxSmallDim) {
+            // the block-level kernel switches to the Clenshaw recurrence when cheb_m is set
+            PM_CUDA(forward_launch(ctx, fp64, p, grid, warps, smem, tc));
+        } else {
+            if (fused_blocks_per_sm(ctx->dpad, fp64, ig, warps, smem, 1) <= 0)
+                return set_err(ctx, PARAMENT_ERR_CUDA, "occupancy query failed (Chebyshev kernel)");
+            PM_CUDA(fused_dispatch(ctx->dpad, fp64, ig, p, grid, warps, smem, ctx->stream, 1));
+        }
     } else {
         PM_CUDA(forward_launch(ctx, fp64, p, grid, warps, smem, tc));
     }

@@ -403,13 +403,18 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
     unsigned long long n_exp = 0;
     int m_max = 0, s_max = 0;
 
+    // the paper's Chebyshev exponential (Sec. 2.1, Algorithm 1) when the pre-pass set its degree
+    const bool cheb = p.cheb_m != nullptr;
+    const int mch = cheb ? *p.cheb_m : 0;
+    const Real ib = cheb ? (Real)*p.cheb_inv_beta : Real(0);
+
     for (int t = 0; t < len; ++t) {
         const int64_t j = j0 + t;
         if (tid == 0) {
             slice_coefficients<Real, INTEG, 1>(p, j, true, gam);
             double nu = 0.0;
             for (int e = 0; e < nb; ++e) nu = fma(fabs((double)gam[e]), p.bnorm1[e], nu);
-            s_code = p.cls_code[find_class(p, nu, &flags)];
+            s_code = cheb ? 0 : p.cls_code[find_class(p, nu, &flags)];  // Chebyshev: one degree, set before
         }
         __syncthreads();
         const int code = s_code;
@@ -432,15 +437,59 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
             for (int u = 0; u < 4; ++u) gpk[i * GLD + jj + u] = v[u];
         }
         __syncthreads();
-        // Hermitian unpack into A = -i G / 2^s (upper triangle: Re, strict lower: Im)
+        // Hermitian unpack (upper triangle: Re, strict lower: Im) into A = -i G / 2^s, or into
+        // X = G / beta for the Chebyshev series
         for (int e = tid; e < DD; e += kLargeThreads) {
             const int i = e / D, jj = e % D;
             const Real a = gpk[i * GLD + jj], b = gpk[jj * GLD + i];
             const Real re = (i <= jj) ? a : b;
             const Real im = (i > jj) ? a : ((i < jj) ? -b : Real(0));
-            SX[e] = Cx<Real>::make(im * sc, -re * sc);
+            SX[e] = cheb ? Cx<Real>::make(re * ib, im * ib) : Cx<Real>::make(im * sc, -re * sc);
         }
         __syncthreads();
+        if (cheb) {
+            // Clenshaw: D_m = a_m I, D_{m+1} = 0; D_k = a_k I + 2 X D_{k+1} - D_{k+2}; U = D_0 - D_2
+            const C *ak = (const C *)p.cheb_coef;
+            C *d1 = SX2, *d2 = SX3, *nw = P0;
+            for (int e = tid; e < DD; e += kLargeThreads) {
+                const bool diag = (e / D) == (e % D);
+                d1[e] = diag ? ak[mch] : Cx<Real>::make(Real(0), Real(0));
+                d2[e] = Cx<Real>::make(Real(0), Real(0));
+            }
+            __syncthreads();
+            for (int k = mch - 1; k >= 0; --k) {
+                large_mm<Real, D, TCM>(SX, d1, nw, panels, uc);
+                const C a_k = ak[k];
+                for (int e = tid; e < DD; e += kLargeThreads) {
+                    const C x = nw[e], y = d2[e];
+                    C v = Cx<Real>::make(Real(2) * x.x - y.x, Real(2) * x.y - y.y);
+                    if ((e / D) == (e % D)) {
+                        v.x += a_k.x;
+                        v.y += a_k.y;
+                    }
+                    nw[e] = (k == 0) ? Cx<Real>::make(v.x - y.x, v.y - y.y) : v;
+                }
+                __syncthreads();
+                if (k > 0) {  // D_{k+2} <- D_{k+1}, D_{k+1} <- D_k
+                    C *t2 = d2;
+                    d2 = d1;
+                    d1 = nw;
+                    nw = t2;
+                }
+            }
+            // leaf product R <- U_j R into P1 (U_j is in one of SX2, SX3, P0), which becomes R
+            large_mm<Real, D, TCM>(nw, SR, P1, panels, uc);
+            {
+                C *old = SR;
+                SR = P1;
+                P1 = old;
+            }
+            if (tid == 0) {
+                n_exp += (unsigned long long)mch;
+                m_max = max(m_max, mch);
+            }
+            continue;
+        }
         if (q >= 2) large_mm<Real, D, TCM>(SX, SX, SX2, panels, uc);
         if (q >= 3) large_mm<Real, D, TCM>(SX2, SX, SX3, panels, uc);
         const C *Xq = (q == 1) ? SX : ((q == 2) ? SX2 : SX3);

@@ -390,11 +390,29 @@ def test_chebyshev_degree_follows_the_bound(prop):
     assert degs[0] < degs[1] < degs[2]
 
 
-def test_chebyshev_needs_small_d(prop):
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+@pytest.mark.parametrize("d", [20, 40, 100, 192])
+def test_chebyshev_large_d_fp64_matches_oracle(prop, integrator, d):
+    """The block-level kernel evaluates the Chebyshev series by Clenshaw with its own products."""
     from paper_2108_07126_gb300 import binding as b
 
-    prob = wl.random_problem(32, 1, 5, "midpoint", seed=1)
+    n = 23 if d <= 64 else 5
+    prob = wl.random_problem(d, 2, n, integrator, seed=1300 + d, g_norm=0.6)
     prop.set_option(b.PARAMENT_OPT_EXP_METHOD, 1)
-    with pytest.raises(b.ParamentError) as e:
-        run(prop, prob, "fp64")
-    assert e.value.status == b.PARAMENT_ERR_UNSUPPORTED
+    U = run(prop, prob, "fp64")
+    assert np.max(np.abs(U - ref(prob))) <= TOL64
+    st = prop.stats()
+    assert st["exp_products"] == st["max_degree"] * n and st["max_squarings"] == 0
+
+
+@pytest.mark.parametrize("d,prec", [(32, "fp32"), (64, "fp32"), (128, "fp32"), (128, "fp32_tc_tf32x3")])
+def test_chebyshev_large_d_fp32_matches_oracle(prop, d, prec):
+    import torch
+
+    from paper_2108_07126_gb300 import binding as b
+
+    n = 101 if d <= 64 else 21
+    prob = wl.random_problem(d, 3, n, "magnus4_gl2", seed=1400 + d, g_norm=0.5)
+    prop.set_option(b.PARAMENT_OPT_EXP_METHOD, 1)
+    U = run(prop, prob, prec, c_dtype=torch.float32, h_dtype=torch.complex64)
+    assert np.max(np.abs(U - ref32(prob))) <= 2 * tol32(d, n)
