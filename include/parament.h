@@ -252,9 +252,10 @@ int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, 
  * out and keeps no reference to it or to psi0 after the call.  Method: one forward pass that keeps
  * every leaf and block product, exclusive FP64 prefix scans over them (as for the gradient), then a
  * second pass in which every leaf starts from its prefix and writes its running product at the
- * output slices.  Taylor exponential, FP64 or FP32, d <= 16, every integrator.  N = 0 writes
- * nothing (out may then be NULL).  Errors: INVALID_VALUE for a null out or every < 1; UNSUPPORTED for d > 16, tensor-core
- * precisions or the Chebyshev option; STATE before set_controls.
+ * output slices.  Taylor exponential, FP64 or FP32, every d and integrator (d > 16: one leaf
+ * per thread block, FP64 prefixes by a Hillis-Steele scan over the leaf products).  N = 0 writes
+ * nothing (out may then be NULL).  Errors: INVALID_VALUE for a null out or every < 1; UNSUPPORTED for
+ * tensor-core precisions or the Chebyshev option; STATE before set_controls.
  */
 int parament_propagate_trajectory(parament_ctx *ctx, const void *psi0, void *out, int64_t every,
                                   parament_precision prec);

@@ -39,7 +39,8 @@ PM_DECL_D(16)
 #define PM_DECL_L(D)                                                                                     \
     cudaError_t large_dispatch_d##D(int, int, const FusedParams &, void *, int, size_t, cudaStream_t, int); \
     int large_blocks_per_sm_d##D(int, int, size_t, int);                                                 \
-    size_t large_smem_d##D(int, int, int);
+    size_t large_smem_d##D(int, int, int);                                                               \
+    cudaError_t large_prefix_d##D(const double2 *, int, double2 *, double2 *, double2 **, cudaStream_t);
 PM_DECL_L(32)
 PM_DECL_L(64)
 PM_DECL_L(128)
@@ -591,6 +592,15 @@ cudaError_t large_dispatch(int Dp, int fp64, int integ, const FusedParams &p, vo
         case 64: return large_dispatch_d64(fp64, integ, p, scratch, grid, smem, st, tc);
         case 128: return large_dispatch_d128(fp64, integ, p, scratch, grid, smem, st, tc);
         case 256: return large_dispatch_d256(fp64, integ, p, scratch, grid, smem, st, tc);
+    }
+    return cudaErrorInvalidValue;
+}
+cudaError_t large_prefix(int Dp, const double2 *leaf, int n, double2 *a, double2 *b, double2 **x, cudaStream_t st) {
+    switch (Dp) {
+        case 32: return large_prefix_d32(leaf, n, a, b, x, st);
+        case 64: return large_prefix_d64(leaf, n, a, b, x, st);
+        case 128: return large_prefix_d128(leaf, n, a, b, x, st);
+        case 256: return large_prefix_d256(leaf, n, a, b, x, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -1286,8 +1296,6 @@ int parament_propagate_trajectory(parament_ctx *ctx, const void *psi0, void *out
     if (!out && ctx->n_steps > 0) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "null out");
     if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32)
         return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "trajectory precision must be FP64 or FP32");
-    if (ctx->dpad > kMaxSmallDim)
-        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "trajectories cover d <= %d", kMaxSmallDim);
     if (ctx->opt_exp_method != 0)
         return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "trajectories use the Taylor exponential");
     DeviceGuard guard(ctx->device);
@@ -1339,6 +1347,28 @@ int parament_propagate_trajectory(parament_ctx *ctx, const void *psi0, void *out
     if ((st = forward_setup(ctx, fp64, ctx->uout.ptr, p, grid, warps, smem, lpb))) return st;
     const int64_t L = (int64_t)grid * lpb;
     if ((st = ws_reserve(ctx, ctx->gleaf, (size_t)L * DD * sizeof(double2)))) return st;
+    if (Dp > kMaxSmallDim) {
+        // block-level kernel: one leaf per block; FP64 prefix scan over the leaf products
+        if ((st = ws_reserve(ctx, ctx->gpin, 2 * (size_t)L * DD * sizeof(double2)))) return st;
+        p.leaf_out = (double2 *)ctx->gleaf.ptr;
+        PM_CUDA(forward_launch(ctx, fp64, p, grid, warps, smem));
+        record_launch(ctx, ctx->nb_eff, grid, warps, lpb);
+        double2 *pin = nullptr;
+        PM_CUDA(large_prefix(Dp, (const double2 *)ctx->gleaf.ptr, (int)L, (double2 *)ctx->gpin.ptr,
+                             (double2 *)ctx->gpin.ptr + (size_t)L * DD, &pin, ctx->stream));
+        FusedParams pt = p;
+        pt.leaf_out = nullptr;
+        pt.traj_pin = pin;
+        pt.traj_out = odst;
+        pt.traj_psi0 = psi_dev;
+        pt.traj_every = every;
+        PM_CUDA(forward_launch(ctx, fp64, pt, grid, warps, smem));
+        if (host_out) {
+            PM_CUDA(cudaMemcpyAsync(out, odst, obytes, cudaMemcpyDeviceToHost, ctx->stream));
+            PM_CUDA(cudaStreamSynchronize(ctx->stream));
+        }
+        return PARAMENT_OK;
+    }
     if ((st = ws_reserve(ctx, ctx->gblock, (size_t)grid * DD * sizeof(double2)))) return st;
     if ((st = ws_reserve(ctx, ctx->gbpin, 2 * (size_t)grid * DD * sizeof(double2)))) return st;
     if ((st = ws_reserve(ctx, ctx->gpin, 2 * (size_t)L * DD * sizeof(double2)))) return st;

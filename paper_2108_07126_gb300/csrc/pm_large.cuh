@@ -398,7 +398,16 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
     const int64_t j0 = p.n_steps * blk / nblk;
     const int len = (int)(p.n_steps * (blk + 1) / nblk - j0);
 
-    for (int e = tid; e < DD; e += kLargeThreads) SR[e] = Cx<Real>::make((e / D) == (e % D) ? Real(1) : Real(0), Real(0));
+    // R = I, or in trajectory mode the product of every slice before the leaf (FP64 prefix)
+    const bool traj = p.traj_out != nullptr;
+    for (int e = tid; e < DD; e += kLargeThreads) {
+        if (traj) {
+            const double2 v = p.traj_pin[(size_t)blk * DD + e];
+            SR[e] = Cx<Real>::make((Real)v.x, (Real)v.y);
+        } else {
+            SR[e] = Cx<Real>::make((e / D) == (e % D) ? Real(1) : Real(0), Real(0));
+        }
+    }
     unsigned flags = 0;
     unsigned long long n_exp = 0;
     int m_max = 0, s_max = 0;
@@ -546,11 +555,44 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
             P0 = cur;
             P1 = old;
         }
+        // trajectory mode: R = U(t_{j+1}); keep it at the output slices (R is complete: the
+        // product ends with a block barrier)
+        if (traj && ((j + 1) % p.traj_every == 0 || j + 1 == p.n_steps)) {
+            const int64_t o = j / p.traj_every;
+            const int d = p.d_out;
+            if (p.traj_psi0 == nullptr) {
+                for (int e = tid; e < d * d; e += kLargeThreads) {
+                    const C v = SR[(e / d) * D + e % d];
+                    const size_t at = (size_t)o * d * d + e;
+                    if (p.out_c128) ((double2 *)p.traj_out)[at] = make_double2((double)v.x, (double)v.y);
+                    else ((float2 *)p.traj_out)[at] = make_float2((float)v.x, (float)v.y);
+                }
+            } else {
+                for (int i = tid; i < d; i += kLargeThreads) {
+                    Real re = 0, im = 0;
+                    for (int k = 0; k < d; ++k) {
+                        const C a = SR[i * D + k];
+                        const double2 b = p.traj_psi0[k];
+                        re = fma(a.x, (Real)b.x, fma(-a.y, (Real)b.y, re));
+                        im = fma(a.x, (Real)b.y, fma(a.y, (Real)b.x, im));
+                    }
+                    const size_t at = (size_t)o * d + i;
+                    if (p.out_c128) ((double2 *)p.traj_out)[at] = make_double2((double)re, (double)im);
+                    else ((float2 *)p.traj_out)[at] = make_float2((float)re, (float)im);
+                }
+            }
+        }
         if (tid == 0) {
             n_exp += (unsigned long long)((q - 1) + (rh - 1) + s);
             m_max = max(m_max, cls_m(code));
             s_max = max(s_max, s);
         }
+    }
+
+    // trajectory mode: the forward pass already combined the leaves and recorded statistics
+    if (traj) {
+        __syncthreads();
+        return;
     }
 
     // FP32: one Newton-Schulz step of the polar iteration on the leaf product,
@@ -747,6 +789,81 @@ __global__ void __launch_bounds__(256) tree_level_kernel(const double2 *__restri
     }
 }
 
+// Exclusive prefixes of the leaf products for the trajectory pass, by a Hillis-Steele scan in
+// FP64: x_0 = I, x_b = leaf_{b-1}; at each level out_i = in_i in_{i-off} for i >= off (the later
+// factor on the left), off = 1, 2, 4, ...; the result is prefix_b = leaf_{b-1} ... leaf_0.
+template <int D>
+__global__ void __launch_bounds__(256) prefix_init_kernel(const double2 *__restrict__ leaf, int n,
+                                                          double2 *__restrict__ x) {
+    const size_t DD = (size_t)D * D;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * DD; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = e / DD, t = e % DD;
+        x[e] = (b == 0) ? make_double2((t / D) == (t % D) ? 1.0 : 0.0, 0.0) : leaf[(b - 1) * DD + t];
+    }
+}
+
+// one level: block (tile, i) computes one 32 x 32 tile of out_i
+template <int D>
+__global__ void __launch_bounds__(256) prefix_level_kernel(const double2 *__restrict__ in, int n, int off,
+                                                           double2 *__restrict__ out) {
+    constexpr int T = 32, KP = 16;
+    __shared__ double2 As[T][KP + 1], Bs[KP][T + 1];
+    const int tiles = D / T;
+    const int ti = blockIdx.x / tiles, tj = blockIdx.x % tiles, i = blockIdx.y;
+    const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+    const size_t DD = (size_t)D * D;
+    const double2 *Lt = in + (size_t)i * DD;  // later factor (left)
+    double2 *O = out + (size_t)i * DD;
+    if (i < off) {
+        for (int e = threadIdx.x; e < T * T; e += blockDim.x) {
+            const size_t at = (size_t)(ti * T + e / T) * D + tj * T + e % T;
+            O[at] = Lt[at];
+        }
+        return;
+    }
+    const double2 *Rt = in + (size_t)(i - off) * DD;  // earlier factor (right)
+    double2 acc[2][2] = {{make_double2(0.0, 0.0), make_double2(0.0, 0.0)}, {make_double2(0.0, 0.0), make_double2(0.0, 0.0)}};
+    for (int k0 = 0; k0 < D; k0 += KP) {
+        for (int e = threadIdx.x; e < T * KP; e += blockDim.x) {
+            const int r = e / KP, k = e % KP;
+            As[r][k] = Lt[(size_t)(ti * T + r) * D + k0 + k];
+            const int kb = e / T, cb = e % T;
+            Bs[kb][cb] = Rt[(size_t)(k0 + kb) * D + tj * T + cb];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            const double2 a0 = As[ty][k], a1 = As[ty + 16][k], b0 = Bs[k][tx], b1 = Bs[k][tx + 16];
+            cfma(acc[0][0], a0, b0);
+            cfma(acc[0][1], a0, b1);
+            cfma(acc[1][0], a1, b0);
+            cfma(acc[1][1], a1, b1);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) O[(size_t)(ti * T + ty + 16 * r) * D + tj * T + tx + 16 * c] = acc[r][c];
+}
+
+// exclusive prefixes of n leaf products into x (one of the two buffers a, b; returned)
+template <int D>
+cudaError_t leaf_prefixes(const double2 *leaf, int n, double2 *a, double2 *b, double2 **x, cudaStream_t st) {
+    prefix_init_kernel<D><<<1024, 256, 0, st>>>(leaf, n, a);
+    cudaError_t e = cudaGetLastError();
+    double2 *cur = a, *nxt = b;
+    for (int off = 1; off < n && e == cudaSuccess; off <<= 1) {
+        prefix_level_kernel<D><<<dim3((D / 32) * (D / 32), n), 256, 0, st>>>(cur, n, off, nxt);
+        e = cudaGetLastError();
+        double2 *t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    *x = cur;
+    return e;
+}
+
 // Forward kernel, then the tree levels: FP64 products for the top three levels (and everywhere in
 // FP64 mode), Real products below.  The per-block scratch doubles as the second tree buffer.
 template <typename Real, int D, int INTEG, bool TC = false>
@@ -756,6 +873,7 @@ cudaError_t launch_large(const FusedParams &p, void *scratch, int grid, size_t s
     if (e != cudaSuccess) return e;
     k<<<grid, kLargeThreads, smem, st>>>(p, scratch);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (p.traj_out) return cudaSuccess;  // trajectory pass: no tree
     double2 *bufs[2] = {p.partials, (double2 *)scratch};
     int cur = 0, n = grid;
     do {

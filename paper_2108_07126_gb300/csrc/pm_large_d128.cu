@@ -50,6 +50,10 @@ int large_blocks_per_sm_d128(int fp64, int integ, size_t smem, int tc) {
     return e == cudaSuccess ? nb : 0;
 }
 
+cudaError_t large_prefix_d128(const double2 *leaf, int n, double2 *a, double2 *b, double2 **x, cudaStream_t st) {
+    return leaf_prefixes<128>(leaf, n, a, b, x, st);
+}
+
 size_t large_smem_d128(int fp64, int n_basis, int tc) {
     if (fp64) return large_smem_bytes<double, 128>(n_basis);
     return tc ? large_smem_bytes<float, 128, large_tcm<float, 128, true>()>(n_basis) : large_smem_bytes<float, 128>(n_basis);

@@ -50,6 +50,10 @@ int large_blocks_per_sm_d256(int fp64, int integ, size_t smem, int tc) {
     return e == cudaSuccess ? nb : 0;
 }
 
+cudaError_t large_prefix_d256(const double2 *leaf, int n, double2 *a, double2 *b, double2 **x, cudaStream_t st) {
+    return leaf_prefixes<256>(leaf, n, a, b, x, st);
+}
+
 size_t large_smem_d256(int fp64, int n_basis, int tc) {
     if (fp64) return large_smem_bytes<double, 256>(n_basis);
     return tc ? large_smem_bytes<float, 256, large_tcm<float, 256, true>()>(n_basis) : large_smem_bytes<float, 256>(n_basis);

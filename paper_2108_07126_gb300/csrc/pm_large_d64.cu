@@ -50,6 +50,10 @@ int large_blocks_per_sm_d64(int fp64, int integ, size_t smem, int tc) {
     return e == cudaSuccess ? nb : 0;
 }
 
+cudaError_t large_prefix_d64(const double2 *leaf, int n, double2 *a, double2 *b, double2 **x, cudaStream_t st) {
+    return leaf_prefixes<64>(leaf, n, a, b, x, st);
+}
+
 size_t large_smem_d64(int fp64, int n_basis, int tc) {
     if (fp64) return large_smem_bytes<double, 64>(n_basis);
     return tc ? large_smem_bytes<float, 64, large_tcm<float, 64, true>()>(n_basis) : large_smem_bytes<float, 64>(n_basis);

@@ -191,10 +191,54 @@ def test_errors_and_empty_run(prop, torch):
         assert b.raw_call("parament_set_hamiltonians", ctx, 32, 0, H32.data_ptr(), None, 1, 0) == b.PARAMENT_OK
         assert b.raw_call("parament_set_controls", ctx, None, 1, 4, 0.5) == b.PARAMENT_OK
         big = torch.zeros(4, 32, 32, dtype=torch.complex128, device="cuda")
-        assert b.raw_call("parament_propagate_trajectory", ctx, None, big.data_ptr(), 1, 0) == \
-            b.PARAMENT_ERR_UNSUPPORTED
+        assert b.raw_call("parament_propagate_trajectory", ctx, None, big.data_ptr(), 1, 3) == \
+            b.PARAMENT_ERR_UNSUPPORTED  # tensor-core precision
+        assert b.raw_call("parament_propagate_trajectory", ctx, None, big.data_ptr(), 1, 0) == b.PARAMENT_OK
+        torch.cuda.synchronize()
+        for n in range(4):  # H = I at d = 32 (block-level kernel)
+            assert np.max(np.abs(big[n].cpu().numpy() - np.eye(32) * np.exp(-1j * 0.5 * (n + 1)))) <= TOL64
     finally:
         b.parament_destroy(ctx)
+
+
+@pytest.mark.parametrize("integrator", INTEGRATORS)
+@pytest.mark.parametrize("d,n,every", [(20, 37, 5), (40, 100, 7), (64, 33, 33), (128, 9, 2), (192, 5, 3)])
+def test_large_d_fp64_trajectory_matches_oracle(prop, integrator, d, n, every):
+    """d > 16: one leaf per thread block, FP64 prefixes by a scan over the leaf products."""
+    prob = wl.random_problem(d, 2, n, integrator, seed=2600 + d + n, g_norm=0.5)
+    load(prop, prob, "fp64")
+    T = prop.propagate_trajectory("fp64", every).cpu().numpy()
+    R = oracle.trajectory(prob.H0, prob.Hk, prob.c, prob.dt, integrator, every)
+    assert T.shape == R.shape
+    assert np.max(np.abs(T - R)) <= TOL64
+
+
+@pytest.mark.parametrize("d", [32, 64, 128])
+def test_large_d_fp32_trajectory_and_states(prop, d):
+    n, every = (301, 10) if d <= 64 else (41, 4)
+    prob = wl.random_problem(d, 2, n, "magnus4_gl2", seed=2700 + d, g_norm=0.4)
+    psi0 = wl.haar_unitary(np.random.default_rng(2701 + d), d)[:, 0]
+    load(prop, prob, "fp32")
+    T = prop.propagate_trajectory("fp32", every).cpu().numpy().astype(np.complex128)
+    P = prop.propagate_trajectory("fp32", every, psi0=psi0).cpu().numpy().astype(np.complex128)
+    H0, Hk, c = rounded(prob)
+    R = oracle.trajectory(H0, Hk, c, prob.dt, prob.integrator, every)
+    assert np.max(np.abs(T - R)) <= tol32(d, n)
+    assert np.max(np.abs(P - R @ psi0.astype(np.complex64).astype(np.complex128))) <= tol32(d, n)
+    U = prop.propagate("fp32").cpu().numpy().astype(np.complex128)
+    assert np.max(np.abs(T[-1] - U)) <= 2 * tol32(d, n)
+
+
+@pytest.mark.parametrize("grid", [1, 3, 152])
+def test_large_d_trajectory_independent_of_leaf_count(prop, grid):
+    from paper_2108_07126_gb300 import binding as b
+
+    prob = wl.random_problem(48, 2, 160, "midpoint", seed=2800, g_norm=0.5)
+    R = oracle.trajectory(prob.H0, prob.Hk, prob.c, prob.dt, prob.integrator, 9)
+    prop.set_option(b.PARAMENT_OPT_GRID_BLOCKS, grid)
+    load(prop, prob, "fp64")
+    T = prop.propagate_trajectory("fp64", 9).cpu().numpy()
+    assert np.max(np.abs(T - R)) <= TOL64
 
 
 def test_coupled_spins_trajectory_slice_of_run(prop):
