@@ -320,7 +320,7 @@ def secondary_workloads(torch, b, wl, dev, flush, steps=10, warmup=3):
     small = wl.dense_stress(n_steps=1 << 12)
     res = {}
     for name, prb in (("full", prob), ("small", small)):
-        for prec in ("fp32", "fp32_tc_tf32x3") + (("fp64",) if name == "small" else ()):
+        for prec in ("fp32", "fp32_tc_tf32x3", "fp32_tc_bf16x3") + (("fp64",) if name == "small" else ()):
             cdt = torch.complex128 if prec == "fp64" else torch.complex64
             rdt = torch.float64 if prec == "fp64" else torch.float32
             prop.set_hamiltonians(torch.as_tensor(prb.H0).to(cdt), torch.as_tensor(prb.Hk).to(cdt), prb.integrator)
@@ -331,7 +331,7 @@ def secondary_workloads(torch, b, wl, dev, flush, steps=10, warmup=3):
             res[(name, prec)] = (statistics.mean(per), U.cpu().numpy().astype(np.complex128), st)
     U64s = res[("small", "fp64")][1]
     d128 = {}
-    for prec in ("fp32", "fp32_tc_tf32x3"):
+    for prec in ("fp32", "fp32_tc_tf32x3", "fp32_tc_bf16x3"):
         ms, _, st = res[("full", prec)]
         fl = flops_per_launch(st)
         d128[prec] = {"steps_per_s": prob.n_steps / (ms * 1e-3), "ms": ms, "algorithmic_tflops": fl / (ms * 1e-3) / 1e12,
@@ -345,6 +345,14 @@ def secondary_workloads(torch, b, wl, dev, flush, steps=10, warmup=3):
     d128["fp32_tc_tf32x3"]["roofline"] = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
                                            "frac": ach / tf32_peak, "kernel": "large_kernel<float, 128, GL4, tcgen05>",
                                            "peak_note": "TF32 = measured bf16 burst x 1.1 / 2.25 (of measured)"}
+    # split BF16x3: six BF16 MMAs per real product (b0 b0, b0 b1, b1 b0, b0 b2, b1 b1, b2 b0)
+    st = res[("full", "fp32_tc_bf16x3")][2]
+    n_prod = st["exp_products"] + st["tree_products"] + 2 * st["grid_blocks"]
+    bf16_peak = PEAKS.get("bf16_tflops", 1900.0)
+    ach = 6.0 * 8.0 * 128 ** 3 * n_prod / (res[("full", "fp32_tc_bf16x3")][0] * 1e-3) / 1e12
+    d128["fp32_tc_bf16x3"]["roofline"] = {"bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
+                                           "frac": ach / bf16_peak, "kernel": "large_kernel<float, 128, GL4, tcgen05 bf16>",
+                                           "peak_note": "measured bf16 burst (of measured)"}
     ms, _, st = res[("small", "fp64")]
     d128["fp64"] = {"steps_per_s": small.n_steps / (ms * 1e-3), "ms_N4096": ms,
                     "algorithmic_tflops": flops_per_launch(st) / (ms * 1e-3) / 1e12}

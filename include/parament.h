@@ -91,7 +91,13 @@ typedef enum {
  *        d in 129..256 (and the batched kernel's d = 128): mma.sync; d in 17..64:
  *        the shared-memory CUDA-core product of FP32, which is faster there (and
  *        at least as accurate).  d <= 16: PARAMENT_ERR_UNSUPPORTED.
- *  FP32_TC_BF16X3: not implemented in this build (PARAMENT_ERR_UNSUPPORTED).
+ *  FP32_TC_BF16X3: FP32 with every operand split into three round-to-nearest
+ *        BF16 terms (x = b0 + b1 + b2, 24 significant bits) and the six products
+ *        b0 b0 + b0 b1 + b1 b0 + b0 b2 + b1 b1 + b2 b0 per real product on the
+ *        tensor cores (tcgen05 kind::f16), FP32 accumulation with a fresh
+ *        accumulator per k-chunk.  d in 65..128: tcgen05; d in 17..64: the
+ *        shared-memory CUDA-core product of FP32 (faster there); d <= 16 or
+ *        d > 128: PARAMENT_ERR_UNSUPPORTED.
  */
 typedef enum {
     PARAMENT_PREC_FP64 = 0,

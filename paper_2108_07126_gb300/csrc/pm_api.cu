@@ -1063,15 +1063,16 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) 
     ctx->err.clear();
     if (ctx->state < 2) return set_err(ctx, PARAMENT_ERR_STATE, "set_hamiltonians and set_controls must come first");
     if (!U_out) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "null U_out");
-    if (prec == PARAMENT_PREC_FP32_TC_BF16X3)
-        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "split-BF16 tensor-core products are not in this build");
-    if (prec == PARAMENT_PREC_FP32_TC_TF32X3 && ctx->dpad <= kMaxSmallDim)
-        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "tensor-core products are used for d >= 32 only");
-    if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32 && prec != PARAMENT_PREC_FP32_TC_TF32X3)
+    const bool tc_prec = prec == PARAMENT_PREC_FP32_TC_TF32X3 || prec == PARAMENT_PREC_FP32_TC_BF16X3;
+    if (tc_prec && ctx->dpad <= kMaxSmallDim)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "tensor-core products are used for d > %d only", kMaxSmallDim);
+    if (prec == PARAMENT_PREC_FP32_TC_BF16X3 && ctx->dpad > 128)
+        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "split-BF16x3 products are built for d <= 128");
+    if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32 && !tc_prec)
         return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown precision %d", (int)prec);
     DeviceGuard guard(ctx->device);
     const int fp64 = prec == PARAMENT_PREC_FP64;
-    const int tc = prec == PARAMENT_PREC_FP32_TC_TF32X3;
+    const int tc = prec == PARAMENT_PREC_FP32_TC_TF32X3 ? 1 : (prec == PARAMENT_PREC_FP32_TC_BF16X3 ? 2 : 0);
 
     const size_t esz = ctx->dtype == PARAMENT_C128 ? 16 : 8;
     const bool host_out = !is_device_ptr(U_out);

@@ -49,14 +49,15 @@ template <typename Real, int D> struct LGeo {
 
 template <int D> struct TcGeo;
 
-// TCM: 0 = CUDA-core products, 1 = 3xTF32 with mma.sync, 2 = 3xTF32 with tcgen05 (D = 128)
+// TCM: 0 = CUDA-core products, 1 = 3xTF32 with mma.sync, 2 = 3xTF32 with tcgen05 (D = 128),
+// 3 = split BF16x3 with tcgen05 (D = 128)
 template <typename Real, int D, int TCM = 0>
 __host__ __device__ inline size_t large_panel_bytes() {
     // the FP64 top tree and the tensor-core products run through the same panels
     size_t b = LGeo<Real, D>::PANEL_BYTES;
     if (LGeo<double, D>::PANEL_BYTES > b) b = LGeo<double, D>::PANEL_BYTES;
     if (TcGeo<D>::PANEL_BYTES > b) b = TcGeo<D>::PANEL_BYTES;
-    if (TCM == 2 && umma::kSmemBytes > b) b = umma::kSmemBytes;
+    if (TCM >= 2 && umma::kSmemBytes > b) b = umma::kSmemBytes;
     return b;
 }
 
@@ -362,7 +363,10 @@ __device__ __forceinline__ void smem_mm(const float2 *__restrict__ A, const floa
 template <typename Real, int D, int TCM>
 __device__ __forceinline__ void large_mm(const typename Cx<Real>::T *A, const typename Cx<Real>::T *B,
                                          typename Cx<Real>::T *Cout, unsigned char *panels, umma::Ctx *uc) {
-    if constexpr (TCM == 2 && D == 128 && std::is_same<Real, float>::value) umma::cmul128(A, B, Cout, panels, *uc);
+    if constexpr (TCM == 2 && D == 128 && std::is_same<Real, float>::value)
+        umma::cmul128<umma::kTF32x3>(A, B, Cout, panels, *uc);
+    else if constexpr (TCM == 3 && D == 128 && std::is_same<Real, float>::value)
+        umma::cmul128<umma::kBF16x3>(A, B, Cout, panels, *uc);
     else if constexpr (TCM >= 1 && std::is_same<Real, float>::value) cta_mm_tc<D>(A, B, Cout, panels);
     else if constexpr (large_resident<Real, D, TCM>()) smem_mm<D>(A, B, Cout);
     else cta_mm<Real, D>(A, B, Cout, panels);
@@ -390,7 +394,7 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
     C *SR = ws + 3 * DD, *P0 = ws + 4 * DD, *P1 = ws + 5 * DD;
     // packed exponent: in shared memory (rows padded to D + 1, conflict-free transposed reads)
     // when the tensor-core stages leave room, else in a free scratch slot
-    constexpr bool kGpkShared = (TCM == 2) || kResident;
+    constexpr bool kGpkShared = (TCM >= 2) || kResident;
     static_assert(DD % (4 * kLargeThreads) == 0, "element passes take four elements per thread and step");
     constexpr int GLD = kGpkShared ? D + 1 : D;
     const Real *packed = (const Real *)p.packed;
@@ -429,7 +433,7 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
         const int code = s_code;
         const int q = cls_q(code), rh = cls_r(code), s = cls_s(code) + p.extra_squarings;
         const Real sc = pow2neg<Real>(s);
-        Real *gpk = (TCM == 2) ? (Real *)panels : (Real *)P0;  // resident: the free slot P0 in shared memory
+        Real *gpk = (TCM >= 2) ? (Real *)panels : (Real *)P0;  // resident: the free slot P0 in shared memory
 
         // packed exponent sum_b gamma_b P_b, four entries per thread and step (independent loads)
         for (int e4 = tid; e4 < DD / 4; e4 += kLargeThreads) {
@@ -642,21 +646,21 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
     __syncthreads();
 }
 
-// products of the 3xTF32 precision in the standalone large kernel: tcgen05 for D = 128, mma.sync
-// for D = 256; at D <= 64 the shared-memory CUDA-core product is faster than both (and at least as
-// accurate) and is used instead
-template <typename Real, int D, bool TC>
+// products of the tensor-core precisions in the standalone large kernel (TC: 0 none, 1 3xTF32,
+// 2 split BF16x3): tcgen05 for D = 128, mma.sync 3xTF32 for D = 256; at D <= 64 the shared-memory
+// CUDA-core product is faster than both (and at least as accurate) and is used instead
+template <typename Real, int D, int TC>
 __host__ __device__ constexpr int large_tcm() {
-    return (!TC || !std::is_same<Real, float>::value || D <= 64) ? 0 : (D == 128 ? 2 : 1);
+    return (TC == 0 || !std::is_same<Real, float>::value || D <= 64) ? 0 : (D == 128 ? (TC == 2 ? 3 : 2) : 1);
 }
 
-template <typename Real, int D, int INTEG, bool TC = false>
+template <typename Real, int D, int INTEG, int TC = 0>
 __global__ void __launch_bounds__(kLargeThreads, 1) large_kernel(const FusedParams p, void *scratch) {
     extern __shared__ __align__(16) unsigned char smem[];
     using C = typename Cx<Real>::T;
     constexpr int TCM = large_tcm<Real, D, TC>();
     C *ws = (C *)scratch + (size_t)blockIdx.x * kLargeSlots * D * D;
-    if constexpr (TCM == 2) {
+    if constexpr (TCM >= 2) {
         __shared__ __align__(8) uint64_t s_mbar[umma::kStages];
         __shared__ uint32_t s_tmem;
         __shared__ int s_abort;
@@ -866,7 +870,7 @@ cudaError_t leaf_prefixes(const double2 *leaf, int n, double2 *a, double2 *b, do
 
 // Forward kernel, then the tree levels: FP64 products for the top three levels (and everywhere in
 // FP64 mode), Real products below.  The per-block scratch doubles as the second tree buffer.
-template <typename Real, int D, int INTEG, bool TC = false>
+template <typename Real, int D, int INTEG, int TC = 0>
 cudaError_t launch_large(const FusedParams &p, void *scratch, int grid, size_t smem, cudaStream_t st) {
     auto k = large_kernel<Real, D, INTEG, TC>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

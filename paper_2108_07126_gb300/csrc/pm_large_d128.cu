@@ -5,11 +5,19 @@ namespace pm {
 
 cudaError_t large_dispatch_d128(int fp64, int integ, const FusedParams &p, void *scratch, int grid, size_t smem,
                                cudaStream_t st, int tc) {
+    if (tc == 2 && !fp64) {  // split BF16x3 on tcgen05
+        switch (integ) {
+            case kMidpoint: return launch_large<float, 128, kMidpoint, 2>(p, scratch, grid, smem, st);
+            case kGL2: return launch_large<float, 128, kGL2, 2>(p, scratch, grid, smem, st);
+            case kSimpson: return launch_large<float, 128, kSimpson, 2>(p, scratch, grid, smem, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (tc && !fp64) {
         switch (integ) {
-            case kMidpoint: return launch_large<float, 128, kMidpoint, true>(p, scratch, grid, smem, st);
-            case kGL2: return launch_large<float, 128, kGL2, true>(p, scratch, grid, smem, st);
-            case kSimpson: return launch_large<float, 128, kSimpson, true>(p, scratch, grid, smem, st);
+            case kMidpoint: return launch_large<float, 128, kMidpoint, 1>(p, scratch, grid, smem, st);
+            case kGL2: return launch_large<float, 128, kGL2, 1>(p, scratch, grid, smem, st);
+            case kSimpson: return launch_large<float, 128, kSimpson, 1>(p, scratch, grid, smem, st);
         }
         return cudaErrorInvalidValue;
     }
@@ -31,11 +39,19 @@ int large_blocks_per_sm_d128(int fp64, int integ, size_t smem, int tc) {
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kLargeThreads, smem);
     };
+    if (tc == 2 && !fp64) {
+        switch (integ) {
+            case kMidpoint: q(large_kernel<float, 128, kMidpoint, 2>); break;
+            case kGL2: q(large_kernel<float, 128, kGL2, 2>); break;
+            case kSimpson: q(large_kernel<float, 128, kSimpson, 2>); break;
+        }
+        return e == cudaSuccess ? nb : 0;
+    }
     if (tc && !fp64) {
         switch (integ) {
-            case kMidpoint: q(large_kernel<float, 128, kMidpoint, true>); break;
-            case kGL2: q(large_kernel<float, 128, kGL2, true>); break;
-            case kSimpson: q(large_kernel<float, 128, kSimpson, true>); break;
+            case kMidpoint: q(large_kernel<float, 128, kMidpoint, 1>); break;
+            case kGL2: q(large_kernel<float, 128, kGL2, 1>); break;
+            case kSimpson: q(large_kernel<float, 128, kSimpson, 1>); break;
         }
         return e == cudaSuccess ? nb : 0;
     }
@@ -56,7 +72,8 @@ cudaError_t large_prefix_d128(const double2 *leaf, int n, double2 *a, double2 *b
 
 size_t large_smem_d128(int fp64, int n_basis, int tc) {
     if (fp64) return large_smem_bytes<double, 128>(n_basis);
-    return tc ? large_smem_bytes<float, 128, large_tcm<float, 128, true>()>(n_basis) : large_smem_bytes<float, 128>(n_basis);
+    if (tc == 2) return large_smem_bytes<float, 128, large_tcm<float, 128, 2>()>(n_basis);
+    return tc ? large_smem_bytes<float, 128, large_tcm<float, 128, 1>()>(n_basis) : large_smem_bytes<float, 128>(n_basis);
 }
 
 }  // namespace pm

@@ -7,9 +7,9 @@ cudaError_t large_dispatch_d64(int fp64, int integ, const FusedParams &p, void *
                                cudaStream_t st, int tc) {
     if (tc && !fp64) {
         switch (integ) {
-            case kMidpoint: return launch_large<float, 64, kMidpoint, true>(p, scratch, grid, smem, st);
-            case kGL2: return launch_large<float, 64, kGL2, true>(p, scratch, grid, smem, st);
-            case kSimpson: return launch_large<float, 64, kSimpson, true>(p, scratch, grid, smem, st);
+            case kMidpoint: return launch_large<float, 64, kMidpoint, 1>(p, scratch, grid, smem, st);
+            case kGL2: return launch_large<float, 64, kGL2, 1>(p, scratch, grid, smem, st);
+            case kSimpson: return launch_large<float, 64, kSimpson, 1>(p, scratch, grid, smem, st);
         }
         return cudaErrorInvalidValue;
     }
@@ -33,9 +33,9 @@ int large_blocks_per_sm_d64(int fp64, int integ, size_t smem, int tc) {
     };
     if (tc && !fp64) {
         switch (integ) {
-            case kMidpoint: q(large_kernel<float, 64, kMidpoint, true>); break;
-            case kGL2: q(large_kernel<float, 64, kGL2, true>); break;
-            case kSimpson: q(large_kernel<float, 64, kSimpson, true>); break;
+            case kMidpoint: q(large_kernel<float, 64, kMidpoint, 1>); break;
+            case kGL2: q(large_kernel<float, 64, kGL2, 1>); break;
+            case kSimpson: q(large_kernel<float, 64, kSimpson, 1>); break;
         }
         return e == cudaSuccess ? nb : 0;
     }
@@ -56,7 +56,7 @@ cudaError_t large_prefix_d64(const double2 *leaf, int n, double2 *a, double2 *b,
 
 size_t large_smem_d64(int fp64, int n_basis, int tc) {
     if (fp64) return large_smem_bytes<double, 64>(n_basis);
-    return tc ? large_smem_bytes<float, 64, large_tcm<float, 64, true>()>(n_basis) : large_smem_bytes<float, 64>(n_basis);
+    return tc ? large_smem_bytes<float, 64, large_tcm<float, 64, 1>()>(n_basis) : large_smem_bytes<float, 64>(n_basis);
 }
 
 }  // namespace pm

@@ -18,20 +18,37 @@
 
 #include <cstdint>
 
+#include <cuda_bf16.h>
+
 #include "pm_common.cuh"
 
 namespace pm {
 namespace umma {
 
 constexpr int kStages = 3;
-constexpr int KC = 16;                         // complex k per stage (two K = 8 MMAs)
-constexpr int kPlaneBytes = 128 * KC * 4;      // 128 rows x 16 TF32 operands
-constexpr int kStageBytes = 8 * kPlaneBytes;   // A: Re hi, Re lo, Im hi, Im lo; then B (as B^T) the same
-constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes;
+constexpr int KC = 16;                         // complex k per stage
 constexpr int kLBO = 128;                      // bytes between core matrices along K
-constexpr int kSBO = (KC / 4) * 128;           // bytes between 8-row groups
 constexpr int kTmemCols = 512;                 // two sets of Re and Im accumulators, 128 columns each
 constexpr long long kWaitCycles = 2000000000ll;
+
+// operand formats: 3xTF32 (two TF32 terms per value, K = 8 per MMA) and split BF16x3 (three BF16
+// terms per value, K = 16 per MMA); a plane holds one term of Re or Im of 128 rows x KC k
+constexpr int kTF32x3 = 0, kBF16x3 = 1;
+template <int F> struct Fmt;
+template <> struct Fmt<kTF32x3> {
+    static constexpr int TERMS = 2, ELEM = 4, KMMA = 8;
+    static constexpr int PLANE = 128 * KC * ELEM;          // 8 KB
+    static constexpr int SBO = (KC * ELEM / 16) * 128;     // 4 core matrices along K per 8 rows
+};
+template <> struct Fmt<kBF16x3> {
+    static constexpr int TERMS = 3, ELEM = 2, KMMA = 16;
+    static constexpr int PLANE = 128 * KC * ELEM;          // 4 KB
+    static constexpr int SBO = (KC * ELEM / 16) * 128;     // 2 core matrices along K per 8 rows
+};
+template <int F> constexpr int stage_bytes() { return 4 * Fmt<F>::TERMS * Fmt<F>::PLANE; }  // A and B, Re and Im
+constexpr int kStageBytes = 64 * 1024;  // the larger of the two formats (3xTF32: 8 planes of 8 KB)
+static_assert(stage_bytes<kTF32x3>() <= kStageBytes && stage_bytes<kBF16x3>() <= kStageBytes, "stage size");
+constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes;
 
 struct Ctx {
     uint32_t tmem;     // tensor-memory base address of the accumulators
@@ -44,22 +61,32 @@ struct Ctx {
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // shared-memory matrix descriptor: K-major, no swizzle, relative leading-dimension offset
+template <int F>
 __device__ __forceinline__ uint64_t desc(uint32_t addr) {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(kLBO >> 4) << 16) | ((uint64_t)(kSBO >> 4) << 32) |
-           ((uint64_t)1 << 46);
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(kLBO >> 4) << 16) |
+           ((uint64_t)(Fmt<F>::SBO >> 4) << 32) | ((uint64_t)1 << 46);
 }
 
-// instruction descriptor: D F32, A and B TF32, both K-major, M = N = 128, optional negated A
+// instruction descriptor: D F32, A and B TF32 (kind::tf32) or BF16 (kind::f16), both K-major,
+// M = N = 128, optional negated A
+template <int F>
 __host__ __device__ constexpr uint32_t idesc(bool neg_a) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(128 >> 3) << 17) |
-           ((uint32_t)(128 >> 4) << 24);
+    return (1u << 4) | ((F == kTF32x3 ? 2u : 1u) << 7) | ((F == kTF32x3 ? 2u : 1u) << 10) | ((neg_a ? 1u : 0u) << 13) |
+           ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
+template <int F>
 __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-        "l"(a), "l"(b), "r"(id), "r"(acc));
+    if constexpr (F == kTF32x3)
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(id), "r"(acc));
+    else
+        asm volatile(
+            "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+            "l"(a), "l"(b), "r"(id), "r"(acc));
 }
 
 __device__ __forceinline__ void commit(uint64_t *bar) {
@@ -140,14 +167,42 @@ __device__ __forceinline__ float tf32_rn(float x) {
 }
 
 // hi = rn_tf32(x), lo = rn_tf32(x - hi) of Re and Im of one complex operand into the four planes
-// at byte offset o.  Rounding both parts to nearest keeps the split unbiased (the tensor core
-// would truncate a raw FP32 operand, and the truncations of all operands shrink them the same way).
+// (Re hi, Re lo, Im hi, Im lo) at byte offset o.  Rounding both parts to nearest keeps the split
+// unbiased (the tensor core would truncate a raw FP32 operand, and the truncations of all operands
+// shrink them the same way).
 __device__ __forceinline__ void put_split(unsigned char *planes, int o, float2 v) {
+    constexpr int P = Fmt<kTF32x3>::PLANE;
     const float hr = tf32_rn(v.x), hi = tf32_rn(v.y);
     *(float *)(planes + o) = hr;
-    *(float *)(planes + kPlaneBytes + o) = tf32_rn(v.x - hr);
-    *(float *)(planes + 2 * kPlaneBytes + o) = hi;
-    *(float *)(planes + 3 * kPlaneBytes + o) = tf32_rn(v.y - hi);
+    *(float *)(planes + P + o) = tf32_rn(v.x - hr);
+    *(float *)(planes + 2 * P + o) = hi;
+    *(float *)(planes + 3 * P + o) = tf32_rn(v.y - hi);
+}
+
+// BF16x3: x = b0 + b1 + b2 with b0 = rn_bf16(x), b1 = rn_bf16(x - b0), b2 = rn_bf16(x - b0 - b1)
+// (the differences are exact in FP32); two consecutive k of Re and Im into the six planes
+// (Re b0, b1, b2, Im b0, b1, b2) at byte offset o, one 4-byte word (two BF16) per plane.
+__device__ __forceinline__ void split3(float x, uint16_t (&b)[3]) {
+    float r = x;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(r);
+        b[t] = __bfloat16_as_ushort(h);
+        r -= __bfloat162float(h);
+    }
+}
+__device__ __forceinline__ void put_split3(unsigned char *planes, int o, float2 v0, float2 v1) {
+    constexpr int P = Fmt<kBF16x3>::PLANE;
+    uint16_t r0[3], r1[3], i0[3], i1[3];
+    split3(v0.x, r0);
+    split3(v1.x, r1);
+    split3(v0.y, i0);
+    split3(v1.y, i1);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+        *(uint32_t *)(planes + t * P + o) = (uint32_t)r0[t] | ((uint32_t)r1[t] << 16);
+        *(uint32_t *)(planes + (3 + t) * P + o) = (uint32_t)i0[t] | ((uint32_t)i1[t] << 16);
+    }
 }
 
 __device__ __forceinline__ void wait_stage(Ctx &cx, int s) {
@@ -167,12 +222,14 @@ __device__ __forceinline__ void wait_stage(Ctx &cx, int s) {
 // tensor-memory sets, and the threads add the finished chunk into FP32 register sums with
 // round-to-nearest while the tensor core works on the next chunk.  Thread (warp w, lane l)
 // owns row 32 (w % 4) + l, columns [64 (w / 4), 64 (w / 4) + 64) of Re C and Im C.
+template <int F>
 static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const float2 *__restrict__ B,
                                             float2 *__restrict__ Cout, unsigned char *stages, Ctx &cx) {
     constexpr int NCH = 128 / KC;
+    constexpr int P = Fmt<F>::PLANE, SBO = Fmt<F>::SBO;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (*(volatile int *)cx.abort) return;  // uniform: set before the last block barrier
-    const uint32_t ID = idesc(false), IDN = idesc(true);
+    const uint32_t ID = idesc<F>(false), IDN = idesc<F>(true);
     const int row = (warp & 3) * 32 + lane, col0 = (warp >> 2) * 64;
     const uint32_t tl = cx.tmem + ((uint32_t)((warp & 3) * 32) << 16);
     float sre[64], sim[64];
@@ -199,17 +256,33 @@ static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const 
         }
         fence_before();
     };
-    // lane -> (row % 8, k % 4) makes the 32 four-byte stores of a warp hit 32 banks; thread's
-    // element i of a chunk: row / column g * 8 + lane % 8, k = kg * 4 + lane / 8 (q = 8 warp + i)
+    // Staging: the 32 lanes of a warp fill one core matrix (8 rows x 16 bytes) of every plane per
+    // store instruction, lane -> (row % 8, 4-byte column), so the 32 stores hit 32 banks.
+    //  3xTF32: thread element i of a chunk: row g * 8 + lane % 8, k = kg * 4 + lane / 8, q = 8 warp + i
+    //  BF16x3: thread element i: row g * 8 + lane % 8, k = 2 kp, 2 kp + 1 with kp = kq * 4 + lane / 8,
+    //          q = 4 warp + i, g = q / 2, kq = q % 2 (two BF16 per 4-byte word)
     float2 ra[8], rb[8];  // the chunk being staged, loaded one chunk ahead
     auto load = [&](int c, float2 (&xa)[8], float2 (&xb)[8]) {
         const int k0 = c * KC;
+        if constexpr (F == kTF32x3) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int q = warp * 8 + i, g = q >> 2, kg = q & 3;
-            const int r = g * 8 + (lane & 7), kk = kg * 4 + (lane >> 3);
-            xa[i] = __ldcg(A + r * 128 + k0 + kk);
-            xb[i] = __ldcg(B + (k0 + kk) * 128 + r);  // B^T: row n = r
+            for (int i = 0; i < 8; ++i) {
+                const int q = warp * 8 + i, g = q >> 2, kg = q & 3;
+                const int r = g * 8 + (lane & 7), kk = kg * 4 + (lane >> 3);
+                xa[i] = __ldcg(A + r * 128 + k0 + kk);
+                xb[i] = __ldcg(B + (k0 + kk) * 128 + r);  // B^T: row n = r
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int q = warp * 4 + i, g = q >> 1, kq = q & 1;
+                const int r = g * 8 + (lane & 7), kk = 2 * (kq * 4 + (lane >> 3));
+                const float4 av = __ldcg(reinterpret_cast<const float4 *>(A + r * 128 + k0 + kk));
+                xa[2 * i] = make_float2(av.x, av.y);
+                xa[2 * i + 1] = make_float2(av.z, av.w);
+                xb[2 * i] = __ldcg(B + (k0 + kk) * 128 + r);
+                xb[2 * i + 1] = __ldcg(B + (k0 + kk + 1) * 128 + r);
+            }
         }
     };
     load(0, ra, rb);
@@ -219,12 +292,22 @@ static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const 
         float2 na[8], nb[8];
         if (c + 1 < NCH) load(c + 1, na, nb);
         unsigned char *st = stages + (size_t)s * kStageBytes;
+        if constexpr (F == kTF32x3) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int q = warp * 8 + i, g = q >> 2, kg = q & 3;
-            const int o = g * kSBO + kg * kLBO + (lane & 7) * 16 + (lane >> 3) * 4;
-            put_split(st, o, ra[i]);
-            put_split(st + 4 * kPlaneBytes, o, rb[i]);
+            for (int i = 0; i < 8; ++i) {
+                const int q = warp * 8 + i, g = q >> 2, kg = q & 3;
+                const int o = g * SBO + kg * kLBO + (lane & 7) * 16 + (lane >> 3) * 4;
+                put_split(st, o, ra[i]);
+                put_split(st + 4 * P, o, rb[i]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int q = warp * 4 + i, g = q >> 1, kq = q & 1;
+                const int o = g * SBO + kq * kLBO + (lane & 7) * 16 + (lane >> 3) * 4;
+                put_split3(st, o, ra[2 * i], ra[2 * i + 1]);
+                put_split3(st + 6 * P, o, rb[2 * i], rb[2 * i + 1]);
+            }
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -237,28 +320,50 @@ static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const 
             fence_after();
             const uint32_t sb = smem_u32(st);
             const uint32_t dr = cx.tmem + (uint32_t)((c & 1) * 256), di = dr + 128;
+            if constexpr (F == kTF32x3) {
 #pragma unroll
-            for (int ks = 0; ks < KC / 8; ++ks) {
-                const uint32_t o = (uint32_t)ks * 2 * kLBO;
-                const uint64_t arh = desc(sb + o), arl = desc(sb + kPlaneBytes + o);
-                const uint64_t aih = desc(sb + 2 * kPlaneBytes + o), ail = desc(sb + 3 * kPlaneBytes + o);
-                const uint64_t brh = desc(sb + 4 * kPlaneBytes + o), brl = desc(sb + 5 * kPlaneBytes + o);
-                const uint64_t bih = desc(sb + 6 * kPlaneBytes + o), bil = desc(sb + 7 * kPlaneBytes + o);
-                const uint32_t acc = ks > 0 ? 1u : 0u;  // fresh accumulator for every chunk
-                // small terms first: Re += Re A Re B - Im A Im B
-                mma(dr, arl, brh, ID, acc);
-                mma(dr, arh, brl, ID, 1u);
-                mma(dr, arh, brh, ID, 1u);
-                mma(dr, ail, bih, IDN, 1u);
-                mma(dr, aih, bil, IDN, 1u);
-                mma(dr, aih, bih, IDN, 1u);
-                // Im += Re A Im B + Im A Re B
-                mma(di, arl, bih, ID, acc);
-                mma(di, arh, bil, ID, 1u);
-                mma(di, arh, bih, ID, 1u);
-                mma(di, ail, brh, ID, 1u);
-                mma(di, aih, brl, ID, 1u);
-                mma(di, aih, brh, ID, 1u);
+                for (int ks = 0; ks < KC / 8; ++ks) {
+                    const uint32_t o = (uint32_t)ks * 2 * kLBO;
+                    const uint64_t arh = desc<F>(sb + o), arl = desc<F>(sb + P + o);
+                    const uint64_t aih = desc<F>(sb + 2 * P + o), ail = desc<F>(sb + 3 * P + o);
+                    const uint64_t brh = desc<F>(sb + 4 * P + o), brl = desc<F>(sb + 5 * P + o);
+                    const uint64_t bih = desc<F>(sb + 6 * P + o), bil = desc<F>(sb + 7 * P + o);
+                    const uint32_t acc = ks > 0 ? 1u : 0u;  // fresh accumulator for every chunk
+                    // small terms first: Re += Re A Re B - Im A Im B
+                    mma<F>(dr, arl, brh, ID, acc);
+                    mma<F>(dr, arh, brl, ID, 1u);
+                    mma<F>(dr, arh, brh, ID, 1u);
+                    mma<F>(dr, ail, bih, IDN, 1u);
+                    mma<F>(dr, aih, bil, IDN, 1u);
+                    mma<F>(dr, aih, bih, IDN, 1u);
+                    // Im += Re A Im B + Im A Re B
+                    mma<F>(di, arl, bih, ID, acc);
+                    mma<F>(di, arh, bil, ID, 1u);
+                    mma<F>(di, arh, bih, ID, 1u);
+                    mma<F>(di, ail, brh, ID, 1u);
+                    mma<F>(di, aih, brl, ID, 1u);
+                    mma<F>(di, aih, brh, ID, 1u);
+                }
+            } else {
+                // one K = 16 step; planes: A Re b0..b2, A Im b0..b2, B Re b0..b2, B Im b0..b2
+                uint64_t ar[3], ai[3], br[3], bi[3];
+#pragma unroll
+                for (int t = 0; t < 3; ++t) {
+                    ar[t] = desc<F>(sb + t * P);
+                    ai[t] = desc<F>(sb + (3 + t) * P);
+                    br[t] = desc<F>(sb + (6 + t) * P);
+                    bi[t] = desc<F>(sb + (9 + t) * P);
+                }
+                // the six terms x_t y_u with t + u <= 2, small first
+                constexpr int TT[6] = {2, 1, 0, 1, 0, 0}, UU[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+                for (int w = 0; w < 6; ++w) mma<F>(dr, ar[TT[w]], br[UU[w]], ID, w > 0 ? 1u : 0u);
+#pragma unroll
+                for (int w = 0; w < 6; ++w) mma<F>(dr, ai[TT[w]], bi[UU[w]], IDN, 1u);
+#pragma unroll
+                for (int w = 0; w < 6; ++w) mma<F>(di, ar[TT[w]], bi[UU[w]], ID, w > 0 ? 1u : 0u);
+#pragma unroll
+                for (int w = 0; w < 6; ++w) mma<F>(di, ai[TT[w]], br[UU[w]], ID, 1u);
             }
             commit(cx.mbar + s);
         }

@@ -274,6 +274,16 @@ def test_tensor_core_tf32x3_matches_oracle(prop, d):
     assert np.max(np.abs(U - ref32(prob))) <= 2 * tol32(d, n)
 
 
+@pytest.mark.parametrize("d", [40, 64, 100, 128])
+def test_tensor_core_bf16x3_matches_oracle(prop, d):
+    """Split BF16x3 on tcgen05 (kind::f16, six products per real product) keeps FP32 accuracy."""
+    n = 301 if d <= 64 else 41
+    prob = wl.random_problem(d, 3, n, "magnus4_gl2", seed=950 + d, g_norm=0.5)
+    U = run(prop, prob, "fp32_tc_bf16x3", c_dtype=__import__("torch").float32,
+            h_dtype=__import__("torch").complex64)
+    assert np.max(np.abs(U - ref32(prob))) <= 2 * tol32(d, n)
+
+
 def test_tensor_core_modes_rejected_where_not_built(prop, torch):
     from paper_2108_07126_gb300 import binding as b
 
@@ -281,7 +291,7 @@ def test_tensor_core_modes_rejected_where_not_built(prop, torch):
     with pytest.raises(b.ParamentError) as e:
         run(prop, prob, "fp32_tc_tf32x3", c_dtype=torch.float32, h_dtype=torch.complex64)
     assert e.value.status == b.PARAMENT_ERR_UNSUPPORTED
-    prob = wl.random_problem(32, 1, 10, "midpoint", seed=1)
+    prob = wl.random_problem(192, 1, 4, "midpoint", seed=1)
     with pytest.raises(b.ParamentError) as e:
         run(prop, prob, "fp32_tc_bf16x3", c_dtype=torch.float32, h_dtype=torch.complex64)
     assert e.value.status == b.PARAMENT_ERR_UNSUPPORTED
