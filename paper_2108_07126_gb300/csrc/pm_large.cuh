@@ -661,7 +661,7 @@ __global__ void __launch_bounds__(kLargeThreads, 1) large_kernel(const FusedPara
     constexpr int TCM = large_tcm<Real, D, TC>();
     C *ws = (C *)scratch + (size_t)blockIdx.x * kLargeSlots * D * D;
     if constexpr (TCM >= 2) {
-        __shared__ __align__(8) uint64_t s_mbar[umma::kStages];
+        __shared__ __align__(8) uint64_t s_mbar[umma::kBars];
         __shared__ uint32_t s_tmem;
         __shared__ int s_abort;
         umma::Ctx cx;

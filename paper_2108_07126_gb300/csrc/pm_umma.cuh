@@ -1,19 +1,23 @@
 // Complex 128 x 128 FP32 matrix product on the 5th-generation tensor cores
-// (tcgen05.mma, accumulators in tensor memory), with FP32 accuracy from the
-// three-term TF32 split (Ootomo & Yokota): x = hi + lo with hi = rn_tf32(x),
-// lo = rn_tf32(x - hi); a b ~ hi_a hi_b + hi_a lo_b + lo_a hi_b.  Re C = Re A Re B - Im A Im B uses the negate-A bit
-// of the instruction descriptor for the second term.
+// (tcgen05.mma, accumulators in tensor memory), with FP32 accuracy from a split
+// of every operand into narrower terms: three-term TF32 (Ootomo & Yokota:
+// x = hi + lo, hi = rn_tf32(x), lo = rn_tf32(x - hi); a b ~ hi hi + hi lo +
+// lo hi) or split BF16x3 (x = b0 + b1 + b2; six products).  Re C = Re A Re B -
+// Im A Im B uses the negate-A bit of the instruction descriptor.
 //
-// One thread block of 256 threads: all threads stage k-chunks of both
-// operands from global memory (L2) into shared memory in the canonical
-// no-swizzle K-major layout (8-row x 16-byte core matrices) as the four
-// planes hi / lo of Re / Im, three stages deep; thread 0 issues the MMAs of a
-// chunk and commits them to the stage's mbarrier.  A chunk accumulates Re C in
-// tensor-memory columns [0, 128) and Im C in [128, 256) of set c % 2 (set 1 at
-// column 256); the threads read the finished set back with tcgen05.ld (warp w
-// reads lanes 32 (w % 4) .. + 31, half of the columns), add it into register
-// sums and finally store C row-major.  Every wait is bounded: after about a second without
-// progress the block records kDevTimeout and skips its remaining products.
+// One thread block of 256 threads, warp-specialised: warps 1..7 stage 16-k
+// chunks of A and B^T from global memory (L2) into three shared-memory stages
+// in the canonical no-swizzle K-major layout (8-row x 16-byte core matrices),
+// one plane per term of Re / Im, and signal a "full" mbarrier; thread 0
+// issues the chunk's MMAs into a fresh accumulator set in tensor memory (two
+// sets of Re / Im x 128 columns) and commits them to the stage's "done"
+// mbarrier; all eight warps read the finished set back with tcgen05.ld (warp w
+// reads lanes 32 (w % 4) .. + 31, half of the columns), add it into FP32
+// register sums with round-to-nearest (the tensor-core accumulator truncates)
+// and release the set on a "free" mbarrier.  Staging, MMA execution and
+// read-back of neighbouring chunks overlap; no block-wide barrier inside the
+// product.  Every wait is bounded: after about a second without progress the
+// block records kDevTimeout and skips its remaining products.
 #pragma once
 
 #include <cstdint>
@@ -50,12 +54,18 @@ constexpr int kStageBytes = 64 * 1024;  // the larger of the two formats (3xTF32
 static_assert(stage_bytes<kTF32x3>() <= kStageBytes && stage_bytes<kBF16x3>() <= kStageBytes, "stage size");
 constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes;
 
+// mbarriers of the product pipeline: done[3] (the MMAs of a stage finished, one tcgen05.commit),
+// full[3] (a stage was written, one arrival per producer warp), free[2] (an accumulator set was
+// read back, one arrival per warp)
+constexpr int kProducerWarps = 7;
+constexpr int kBarDone = 0, kBarFull = 3, kBarFree = 6, kBars = 8;
+
 struct Ctx {
-    uint32_t tmem;     // tensor-memory base address of the accumulators
-    uint64_t *mbar;    // kStages mbarriers in shared memory
-    uint32_t phase;    // bit s: parity of the next completion of barrier s (identical in all threads)
-    int *abort;        // shared: a wait timed out, the remaining products are skipped
-    unsigned *status;  // device status word of the call
+    uint32_t tmem;          // tensor-memory base address of the accumulators
+    uint64_t *bar;          // kBars mbarriers in shared memory
+    uint32_t cnt[kBars];    // completions of each barrier consumed so far (identical in all threads)
+    int *abort;             // shared: a wait timed out, the remaining products are skipped
+    unsigned *status;       // device status word of the call
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -127,11 +137,13 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
 // Block-level set-up and tear-down (all threads of the block call both).
-__device__ __forceinline__ void setup(Ctx &cx, uint64_t *mbar, uint32_t *tmem_slot, int *abort, unsigned *status) {
+__device__ __forceinline__ void setup(Ctx &cx, uint64_t *bar, uint32_t *tmem_slot, int *abort, unsigned *status) {
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(mbar + s)) : "memory");
+        for (int b = 0; b < kBars; ++b) {
+            const int count = b < kBarFull ? 1 : (b < kBarFree ? kProducerWarps : 8);
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar + b)), "r"(count) : "memory");
+        }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         *abort = 0;
     }
@@ -145,8 +157,8 @@ __device__ __forceinline__ void setup(Ctx &cx, uint64_t *mbar, uint32_t *tmem_sl
     __syncthreads();
     fence_after();
     cx.tmem = *tmem_slot;
-    cx.mbar = mbar;
-    cx.phase = 0;
+    cx.bar = bar;
+    for (int b = 0; b < kBars; ++b) cx.cnt[b] = 0;
     cx.abort = abort;
     cx.status = status;
 }
@@ -205,23 +217,21 @@ __device__ __forceinline__ void put_split3(unsigned char *planes, int o, float2 
     }
 }
 
-__device__ __forceinline__ void wait_stage(Ctx &cx, int s) {
-    if (!*(volatile int *)cx.abort && !wait(cx.mbar + s, (cx.phase >> s) & 1u)) {
+// bounded wait for completion number k (0-based) of barrier b
+__device__ __forceinline__ void wait_idx(Ctx &cx, int b, uint32_t k) {
+    if (!*(volatile int *)cx.abort && !wait(cx.bar + b, k & 1u)) {
         *(volatile int *)cx.abort = 1;
         atomicOr(cx.status, kDevTimeout);
     }
-    cx.phase ^= 1u << s;
+}
+
+__device__ __forceinline__ void arrive(uint64_t *bar) {
+    asm volatile("{\n.reg .b64 arrst;\nmbarrier.arrive.shared::cta.b64 arrst, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // C = A B; A, B, C: 128 x 128 complex FP32, row-major, global memory (C may not alias A or B).
-// Called by all 256 threads of the block; `stages` is kSmemBytes of shared memory.
-//
-// The tensor core truncates when it adds a product into its accumulator, so a long
-// accumulation chain is biased (every same-sign sum, e.g. the diagonal of X^2, comes out
-// small).  Each k-chunk therefore starts a fresh accumulator, alternating between two
-// tensor-memory sets, and the threads add the finished chunk into FP32 register sums with
-// round-to-nearest while the tensor core works on the next chunk.  Thread (warp w, lane l)
-// owns row 32 (w % 4) + l, columns [64 (w / 4), 64 (w / 4) + 64) of Re C and Im C.
+// Called by all 256 threads of the block; `stages` is kSmemBytes of shared memory.  Thread
+// (warp w, lane l) owns row 32 (w % 4) + l, columns [64 (w / 4), 64 (w / 4) + 64) of Re C and Im C.
 template <int F>
 static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const float2 *__restrict__ B,
                                             float2 *__restrict__ Cout, unsigned char *stages, Ctx &cx) {
@@ -232,20 +242,26 @@ static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const 
     const uint32_t ID = idesc<F>(false), IDN = idesc<F>(true);
     const int row = (warp & 3) * 32 + lane, col0 = (warp >> 2) * 64;
     const uint32_t tl = cx.tmem + ((uint32_t)((warp & 3) * 32) << 16);
+    // completions of each barrier before this product: chunk c is use c / 3 of stage c % 3 and
+    // use c / 2 of accumulator set c % 2
+    uint32_t base[kBars];
+#pragma unroll
+    for (int b = 0; b < kBars; ++b) base[b] = cx.cnt[b];
     float sre[64], sim[64];
 #pragma unroll
     for (int j = 0; j < 64; ++j) sre[j] = sim[j] = 0.f;
-    // chunk c's partial sums from tensor-memory set c % 2 into the register sums
+
+    // chunk c's partial sums from tensor-memory set c % 2 into the register sums, then release the set
     auto gather = [&](int c) {
-        wait_stage(cx, c % kStages);  // its commit: every MMA of chunk c is done
+        wait_idx(cx, kBarDone + c % kStages, base[kBarDone + c % kStages] + c / kStages);
         fence_after();
-        if (!__syncthreads_or(*(volatile int *)cx.abort)) {  // block-uniform: tcgen05.ld is warp-collective
-            const uint32_t base = tl + (uint32_t)((c & 1) * 256 + col0);
+        if (!__any_sync(0xffffffffu, *(volatile int *)cx.abort)) {  // warp-uniform: tcgen05.ld is collective
+            const uint32_t tb = tl + (uint32_t)((c & 1) * 256 + col0);
 #pragma unroll
             for (int cc = 0; cc < 64; cc += 16) {
                 float re[16], im[16];
-                ld16(base + (uint32_t)cc, re);
-                ld16(base + 128u + (uint32_t)cc, im);
+                ld16(tb + (uint32_t)cc, re);
+                ld16(tb + 128u + (uint32_t)cc, im);
                 wait_ld();
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -255,121 +271,145 @@ static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const 
             }
         }
         fence_before();
+        __syncwarp();
+        if (lane == 0) arrive(cx.bar + kBarFree + (c & 1));
     };
-    // Staging: the 32 lanes of a warp fill one core matrix (8 rows x 16 bytes) of every plane per
-    // store instruction, lane -> (row % 8, 4-byte column), so the 32 stores hit 32 banks.
-    //  3xTF32: thread element i of a chunk: row g * 8 + lane % 8, k = kg * 4 + lane / 8, q = 8 warp + i
-    //  BF16x3: thread element i: row g * 8 + lane % 8, k = 2 kp, 2 kp + 1 with kp = kq * 4 + lane / 8,
-    //          q = 4 warp + i, g = q / 2, kq = q % 2 (two BF16 per 4-byte word)
-    float2 ra[8], rb[8];  // the chunk being staged, loaded one chunk ahead
-    auto load = [&](int c, float2 (&xa)[8], float2 (&xb)[8]) {
-        const int k0 = c * KC;
-        if constexpr (F == kTF32x3) {
+
+    // producer warp p = warp - 1 stages warp-items q = p, p + 7, ... of a chunk; a warp-item fills
+    // one core matrix (8 rows x 16 bytes) of every plane, lane -> (row % 8, 4-byte column), so the
+    // 32 four-byte stores of a store instruction hit 32 banks
+    //  3xTF32: items 0..63 of A, 64..127 of B^T; item (g, kg): rows g * 8 .., k = kg * 4 + lane / 8
+    //  BF16x3: items 0..31 of A, 32..63 of B^T; item (g, kq): k = 2 (kq * 4 + lane / 8) + {0, 1}
+    // The loads of chunk c + 1 go out right after chunk c is published, so their latency overlaps
+    // the read-back of chunk c - 1 and the MMAs of chunk c.
+    constexpr int NIT = (F == kTF32x3) ? (128 + kProducerWarps - 1) / kProducerWarps
+                                       : (64 + kProducerWarps - 1) / kProducerWarps;
+    float2 v0[NIT], v1[NIT];  // the next chunk's operands (v1: second k of a BF16 pair)
+    auto load = [&](int c) {
+        const int p = warp - 1, k0 = c * KC;
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int q = warp * 8 + i, g = q >> 2, kg = q & 3;
-                const int r = g * 8 + (lane & 7), kk = kg * 4 + (lane >> 3);
-                xa[i] = __ldcg(A + r * 128 + k0 + kk);
-                xb[i] = __ldcg(B + (k0 + kk) * 128 + r);  // B^T: row n = r
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int q = warp * 4 + i, g = q >> 1, kq = q & 1;
-                const int r = g * 8 + (lane & 7), kk = 2 * (kq * 4 + (lane >> 3));
-                const float4 av = __ldcg(reinterpret_cast<const float4 *>(A + r * 128 + k0 + kk));
-                xa[2 * i] = make_float2(av.x, av.y);
-                xa[2 * i + 1] = make_float2(av.z, av.w);
-                xb[2 * i] = __ldcg(B + (k0 + kk) * 128 + r);
-                xb[2 * i + 1] = __ldcg(B + (k0 + kk + 1) * 128 + r);
-            }
-        }
-    };
-    load(0, ra, rb);
-    for (int c = 0; c < NCH; ++c) {
-        // stage c % kStages was last read by the MMAs of chunk c - kStages, gathered already
-        const int s = c % kStages;
-        float2 na[8], nb[8];
-        if (c + 1 < NCH) load(c + 1, na, nb);
-        unsigned char *st = stages + (size_t)s * kStageBytes;
-        if constexpr (F == kTF32x3) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int q = warp * 8 + i, g = q >> 2, kg = q & 3;
-                const int o = g * SBO + kg * kLBO + (lane & 7) * 16 + (lane >> 3) * 4;
-                put_split(st, o, ra[i]);
-                put_split(st + 4 * P, o, rb[i]);
-            }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int q = warp * 4 + i, g = q >> 1, kq = q & 1;
-                const int o = g * SBO + kq * kLBO + (lane & 7) * 16 + (lane >> 3) * 4;
-                put_split3(st, o, ra[2 * i], ra[2 * i + 1]);
-                put_split3(st + 6 * P, o, rb[2 * i], rb[2 * i + 1]);
-            }
-        }
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            ra[i] = na[i];
-            rb[i] = nb[i];
-        }
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-        __syncthreads();  // also: set c % 2 was read out (chunk c - 2 gathered) by every thread
-        if (tid == 0) {
-            fence_after();
-            const uint32_t sb = smem_u32(st);
-            const uint32_t dr = cx.tmem + (uint32_t)((c & 1) * 256), di = dr + 128;
+        for (int i = 0; i < NIT; ++i) {
+            const int q = p + kProducerWarps * i;
             if constexpr (F == kTF32x3) {
-#pragma unroll
-                for (int ks = 0; ks < KC / 8; ++ks) {
-                    const uint32_t o = (uint32_t)ks * 2 * kLBO;
-                    const uint64_t arh = desc<F>(sb + o), arl = desc<F>(sb + P + o);
-                    const uint64_t aih = desc<F>(sb + 2 * P + o), ail = desc<F>(sb + 3 * P + o);
-                    const uint64_t brh = desc<F>(sb + 4 * P + o), brl = desc<F>(sb + 5 * P + o);
-                    const uint64_t bih = desc<F>(sb + 6 * P + o), bil = desc<F>(sb + 7 * P + o);
-                    const uint32_t acc = ks > 0 ? 1u : 0u;  // fresh accumulator for every chunk
-                    // small terms first: Re += Re A Re B - Im A Im B
-                    mma<F>(dr, arl, brh, ID, acc);
-                    mma<F>(dr, arh, brl, ID, 1u);
-                    mma<F>(dr, arh, brh, ID, 1u);
-                    mma<F>(dr, ail, bih, IDN, 1u);
-                    mma<F>(dr, aih, bil, IDN, 1u);
-                    mma<F>(dr, aih, bih, IDN, 1u);
-                    // Im += Re A Im B + Im A Re B
-                    mma<F>(di, arl, bih, ID, acc);
-                    mma<F>(di, arh, bil, ID, 1u);
-                    mma<F>(di, arh, bih, ID, 1u);
-                    mma<F>(di, ail, brh, ID, 1u);
-                    mma<F>(di, aih, brl, ID, 1u);
-                    mma<F>(di, aih, brh, ID, 1u);
-                }
+                const int qq = q & 63, g = qq >> 2, kg = qq & 3;
+                const int r = g * 8 + (lane & 7), kk = kg * 4 + (lane >> 3);
+                if (q < 128) v0[i] = (q < 64) ? __ldcg(A + r * 128 + k0 + kk) : __ldcg(B + (k0 + kk) * 128 + r);
             } else {
-                // one K = 16 step; planes: A Re b0..b2, A Im b0..b2, B Re b0..b2, B Im b0..b2
-                uint64_t ar[3], ai[3], br[3], bi[3];
-#pragma unroll
-                for (int t = 0; t < 3; ++t) {
-                    ar[t] = desc<F>(sb + t * P);
-                    ai[t] = desc<F>(sb + (3 + t) * P);
-                    br[t] = desc<F>(sb + (6 + t) * P);
-                    bi[t] = desc<F>(sb + (9 + t) * P);
+                const int qq = q & 31, g = qq >> 1, kq = qq & 1;
+                const int r = g * 8 + (lane & 7), kk = 2 * (kq * 4 + (lane >> 3));
+                if (q < 32) {
+                    const float4 av = __ldcg(reinterpret_cast<const float4 *>(A + r * 128 + k0 + kk));
+                    v0[i] = make_float2(av.x, av.y);
+                    v1[i] = make_float2(av.z, av.w);
+                } else if (q < 64) {
+                    v0[i] = __ldcg(B + (k0 + kk) * 128 + r);
+                    v1[i] = __ldcg(B + (k0 + kk + 1) * 128 + r);
                 }
-                // the six terms x_t y_u with t + u <= 2, small first
-                constexpr int TT[6] = {2, 1, 0, 1, 0, 0}, UU[6] = {0, 1, 2, 0, 1, 0};
-#pragma unroll
-                for (int w = 0; w < 6; ++w) mma<F>(dr, ar[TT[w]], br[UU[w]], ID, w > 0 ? 1u : 0u);
-#pragma unroll
-                for (int w = 0; w < 6; ++w) mma<F>(dr, ai[TT[w]], bi[UU[w]], IDN, 1u);
-#pragma unroll
-                for (int w = 0; w < 6; ++w) mma<F>(di, ar[TT[w]], bi[UU[w]], ID, w > 0 ? 1u : 0u);
-#pragma unroll
-                for (int w = 0; w < 6; ++w) mma<F>(di, ai[TT[w]], br[UU[w]], ID, 1u);
             }
-            commit(cx.mbar + s);
         }
-        if (c >= 1) gather(c - 1);  // overlaps the MMAs of chunk c
+    };
+    auto stage = [&](int c) {
+        const int p = warp - 1;
+        unsigned char *st = stages + (size_t)(c % kStages) * kStageBytes;
+#pragma unroll
+        for (int i = 0; i < NIT; ++i) {
+            const int q = p + kProducerWarps * i;
+            if constexpr (F == kTF32x3) {
+                const int qq = q & 63, g = qq >> 2, kg = qq & 3;
+                const int o = g * SBO + kg * kLBO + (lane & 7) * 16 + (lane >> 3) * 4;
+                if (q < 128) put_split(st + (q < 64 ? 0 : 4 * P), o, v0[i]);
+            } else {
+                const int qq = q & 31, g = qq >> 1, kq = qq & 1;
+                const int o = g * SBO + kq * kLBO + (lane & 7) * 16 + (lane >> 3) * 4;
+                if (q < 64) put_split3(st + (q < 32 ? 0 : 6 * P), o, v0[i], v1[i]);
+            }
+        }
+    };
+
+    // thread 0: the MMAs of chunk c into accumulator set c % 2
+    auto issue = [&](int c) {
+        const int s = c % kStages;
+        const uint32_t sb = smem_u32(stages + (size_t)s * kStageBytes);
+        const uint32_t dr = cx.tmem + (uint32_t)((c & 1) * 256), di = dr + 128;
+        if constexpr (F == kTF32x3) {
+#pragma unroll
+            for (int ks = 0; ks < KC / 8; ++ks) {
+                const uint32_t o = (uint32_t)ks * 2 * kLBO;
+                const uint64_t arh = desc<F>(sb + o), arl = desc<F>(sb + P + o);
+                const uint64_t aih = desc<F>(sb + 2 * P + o), ail = desc<F>(sb + 3 * P + o);
+                const uint64_t brh = desc<F>(sb + 4 * P + o), brl = desc<F>(sb + 5 * P + o);
+                const uint64_t bih = desc<F>(sb + 6 * P + o), bil = desc<F>(sb + 7 * P + o);
+                const uint32_t acc = ks > 0 ? 1u : 0u;  // fresh accumulator for every chunk
+                // small terms first: Re += Re A Re B - Im A Im B
+                mma<F>(dr, arl, brh, ID, acc);
+                mma<F>(dr, arh, brl, ID, 1u);
+                mma<F>(dr, arh, brh, ID, 1u);
+                mma<F>(dr, ail, bih, IDN, 1u);
+                mma<F>(dr, aih, bil, IDN, 1u);
+                mma<F>(dr, aih, bih, IDN, 1u);
+                // Im += Re A Im B + Im A Re B
+                mma<F>(di, arl, bih, ID, acc);
+                mma<F>(di, arh, bil, ID, 1u);
+                mma<F>(di, arh, bih, ID, 1u);
+                mma<F>(di, ail, brh, ID, 1u);
+                mma<F>(di, aih, brl, ID, 1u);
+                mma<F>(di, aih, brh, ID, 1u);
+            }
+        } else {
+            // one K = 16 step; planes: A Re b0..b2, A Im b0..b2, B Re b0..b2, B Im b0..b2
+            uint64_t ar[3], ai[3], br[3], bi[3];
+#pragma unroll
+            for (int t = 0; t < 3; ++t) {
+                ar[t] = desc<F>(sb + t * P);
+                ai[t] = desc<F>(sb + (3 + t) * P);
+                br[t] = desc<F>(sb + (6 + t) * P);
+                bi[t] = desc<F>(sb + (9 + t) * P);
+            }
+            // the six terms x_t y_u with t + u <= 2, small first
+            constexpr int TT[6] = {2, 1, 0, 1, 0, 0}, UU[6] = {0, 1, 2, 0, 1, 0};
+#pragma unroll
+            for (int w = 0; w < 6; ++w) mma<F>(dr, ar[TT[w]], br[UU[w]], ID, w > 0 ? 1u : 0u);
+#pragma unroll
+            for (int w = 0; w < 6; ++w) mma<F>(dr, ai[TT[w]], bi[UU[w]], IDN, 1u);
+#pragma unroll
+            for (int w = 0; w < 6; ++w) mma<F>(di, ar[TT[w]], bi[UU[w]], ID, w > 0 ? 1u : 0u);
+#pragma unroll
+            for (int w = 0; w < 6; ++w) mma<F>(di, ai[TT[w]], br[UU[w]], ID, 1u);
+        }
+        commit(cx.bar + kBarDone + s);
+    };
+
+    if (warp != 0) load(0);
+    for (int c = 0; c < NCH; ++c) {
+        const int s = c % kStages;
+        if (warp != 0) {
+            // stage s was last read by the MMAs of chunk c - 3 (earlier products are drained)
+            if (c >= kStages) wait_idx(cx, kBarDone + s, base[kBarDone + s] + (c - kStages) / kStages);
+            stage(c);
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) arrive(cx.bar + kBarFull + s);
+            if (c + 1 < NCH) load(c + 1);
+        } else if (lane == 0) {
+            wait_idx(cx, kBarFull + s, base[kBarFull + s] + c / kStages);
+            // accumulator set c % 2 was read back by every warp (chunk c - 2)
+            if (c >= 2) wait_idx(cx, kBarFree + (c & 1), base[kBarFree + (c & 1)] + (c - 2) / 2);
+            fence_after();
+            issue(c);
+        }
+        __syncwarp();
+        if (c >= 1) gather(c - 1);  // overlaps the MMAs of chunk c and the staging of chunk c + 1
     }
     gather(NCH - 1);
+    // every thread consumed the same completions: 3, 3, 2 uses of the stages, 4 of each set
+#pragma unroll
+    for (int b = 0; b < kStages; ++b) {
+        const uint32_t uses = (NCH - b + kStages - 1) / kStages;
+        cx.cnt[kBarDone + b] += uses;
+        cx.cnt[kBarFull + b] += uses;
+    }
+    cx.cnt[kBarFree] += NCH / 2;
+    cx.cnt[kBarFree + 1] += NCH / 2;
     if (!__syncthreads_or(*(volatile int *)cx.abort)) {
         float4 *dst = reinterpret_cast<float4 *>(Cout + row * 128 + col0);
 #pragma unroll
