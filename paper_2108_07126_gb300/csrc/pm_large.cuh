@@ -180,11 +180,9 @@ template <int D> struct TcGeo {
     static_assert(WM * WN * 32 == kLargeThreads && MT >= 1 && NT >= 1, "warp tiling");
 };
 
-__device__ __forceinline__ unsigned tf32_rna(float x) {
-    unsigned r;
-    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-    return r;
-}
+// round-to-nearest TF32 bits of x, ties away from zero (half a unit of the 10-bit mantissa added
+// to the magnitude bits, the 13 low bits cleared; finite inputs only)
+__device__ __forceinline__ unsigned tf32_rna(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
 
 __device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
     hi = tf32_rna(x);

@@ -22,8 +22,6 @@
 
 #include <cstdint>
 
-#include <cuda_bf16.h>
-
 #include "pm_common.cuh"
 
 namespace pm {
@@ -78,11 +76,11 @@ __device__ __forceinline__ uint64_t desc(uint32_t addr) {
 }
 
 // instruction descriptor: D F32, A and B TF32 (kind::tf32) or BF16 (kind::f16), both K-major,
-// M = N = 128, optional negated A
+// M = 128, N = 128 or 256, optional negated A
 template <int F>
-__host__ __device__ constexpr uint32_t idesc(bool neg_a) {
+__host__ __device__ constexpr uint32_t idesc(bool neg_a, int n = 128) {
     return (1u << 4) | ((F == kTF32x3 ? 2u : 1u) << 7) | ((F == kTF32x3 ? 2u : 1u) << 10) | ((neg_a ? 1u : 0u) << 13) |
-           ((uint32_t)(128 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+           ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
 template <int F>
@@ -171,49 +169,74 @@ __device__ __forceinline__ void teardown(const Ctx &cx) {
                      : "memory");
 }
 
-// round-to-nearest TF32 value of x (FP32 bit pattern with the low 13 bits clear)
+// round-to-nearest TF32 value of x (ties away from zero): add half a unit of the 10-bit mantissa
+// to the magnitude bits and clear the 13 low bits (integer pipe; a carry moves into the exponent
+// as it should).  Finite inputs only.
 __device__ __forceinline__ float tf32_rn(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
-// hi = rn_tf32(x), lo = rn_tf32(x - hi) of Re and Im of one complex operand into the four planes
-// (Re hi, Re lo, Im hi, Im lo) at byte offset o.  Rounding both parts to nearest keeps the split
+// hi = rn_tf32(x), lo = rn_tf32(x - hi) of Re and Im of four consecutive k of one row into the
+// 16-byte row of a core matrix in four planes, at byte offset o: Re hi at planes + o, then Re lo,
+// Im hi, Im lo at the plane offsets PRL, PIH, PIL.  Rounding both parts to nearest keeps the split
 // unbiased (the tensor core would truncate a raw FP32 operand, and the truncations of all operands
 // shrink them the same way).
-__device__ __forceinline__ void put_split(unsigned char *planes, int o, float2 v) {
-    constexpr int P = Fmt<kTF32x3>::PLANE;
-    const float hr = tf32_rn(v.x), hi = tf32_rn(v.y);
-    *(float *)(planes + o) = hr;
-    *(float *)(planes + P + o) = tf32_rn(v.x - hr);
-    *(float *)(planes + 2 * P + o) = hi;
-    *(float *)(planes + 3 * P + o) = tf32_rn(v.y - hi);
+template <int PRL, int PIH, int PIL>
+__device__ __forceinline__ void put_split(unsigned char *planes, int o, const float2 (&v)[4]) {
+    float4 rh, rl, ih, il;
+    float *prh = &rh.x, *prl = &rl.x, *pih = &ih.x, *pil = &il.x;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        prh[t] = tf32_rn(v[t].x);
+        prl[t] = tf32_rn(v[t].x - prh[t]);
+        pih[t] = tf32_rn(v[t].y);
+        pil[t] = tf32_rn(v[t].y - pih[t]);
+    }
+    *(float4 *)(planes + o) = rh;
+    *(float4 *)(planes + PRL + o) = rl;
+    *(float4 *)(planes + PIH + o) = ih;
+    *(float4 *)(planes + PIL + o) = il;
 }
 
 // BF16x3: x = b0 + b1 + b2 with b0 = rn_bf16(x), b1 = rn_bf16(x - b0), b2 = rn_bf16(x - b0 - b1)
-// (the differences are exact in FP32); two consecutive k of Re and Im into the six planes
-// (Re b0, b1, b2, Im b0, b1, b2) at byte offset o, one 4-byte word (two BF16) per plane.
-__device__ __forceinline__ void split3(float x, uint16_t (&b)[3]) {
-    float r = x;
+// (the differences are exact in FP32).  Round to nearest even: add 0x7FFF plus the lowest kept
+// bit to the FP32 bits and keep the upper half (integer pipe; finite inputs only).
+__device__ __forceinline__ uint32_t bf16_rne_bits(float x) {
+    const uint32_t u = __float_as_uint(x);
+    return (u + 0x7FFFu + ((u >> 16) & 1u)) >> 16;
+}
+// the three terms of x and y, packed two BF16 per word (x in the low half)
+__device__ __forceinline__ void split3_pair(float x, float y, uint32_t (&w)[3]) {
+    float rx = x, ry = y;
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(r);
-        b[t] = __bfloat16_as_ushort(h);
-        r -= __bfloat162float(h);
+        const uint32_t hx = bf16_rne_bits(rx), hy = bf16_rne_bits(ry);
+        w[t] = hx | (hy << 16);
+        rx -= __uint_as_float(hx << 16);
+        ry -= __uint_as_float(hy << 16);
     }
 }
-__device__ __forceinline__ void put_split3(unsigned char *planes, int o, float2 v0, float2 v1) {
-    constexpr int P = Fmt<kBF16x3>::PLANE;
-    uint16_t r0[3], r1[3], i0[3], i1[3];
-    split3(v0.x, r0);
-    split3(v1.x, r1);
-    split3(v0.y, i0);
-    split3(v1.y, i1);
+// eight consecutive k of Re and Im of one row into the 16-byte row of a core matrix in six planes
+// at byte offset o.  RS / IS: bytes between the planes of consecutive terms of Re / Im; IM: offset
+// of the Im planes.
+template <int RS, int IM, int IS>
+__device__ __forceinline__ void put_split3(unsigned char *planes, int o, const float2 (&v)[8]) {
+    uint4 re[3], im[3];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        uint32_t wr[3], wi[3];
+        split3_pair(v[2 * h].x, v[2 * h + 1].x, wr);
+        split3_pair(v[2 * h].y, v[2 * h + 1].y, wi);
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            (&re[t].x)[h] = wr[t];
+            (&im[t].x)[h] = wi[t];
+        }
+    }
 #pragma unroll
     for (int t = 0; t < 3; ++t) {
-        *(uint32_t *)(planes + t * P + o) = (uint32_t)r0[t] | ((uint32_t)r1[t] << 16);
-        *(uint32_t *)(planes + (3 + t) * P + o) = (uint32_t)i0[t] | ((uint32_t)i1[t] << 16);
+        *(uint4 *)(planes + t * RS + o) = re[t];
+        *(uint4 *)(planes + IM + t * IS + o) = im[t];
     }
 }
 
@@ -239,7 +262,7 @@ static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const 
     constexpr int P = Fmt<F>::PLANE, SBO = Fmt<F>::SBO;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (*(volatile int *)cx.abort) return;  // uniform: set before the last block barrier
-    const uint32_t ID = idesc<F>(false), IDN = idesc<F>(true);
+    const uint32_t ID = idesc<F>(false), IDN = idesc<F>(true), ID2 = idesc<F>(false, 256);
     const int row = (warp & 3) * 32 + lane, col0 = (warp >> 2) * 64;
     const uint32_t tl = cx.tmem + ((uint32_t)((warp & 3) * 32) << 16);
     // completions of each barrier before this product: chunk c is use c / 3 of stage c % 3 and
@@ -275,36 +298,36 @@ static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const 
         if (lane == 0) arrive(cx.bar + kBarFree + (c & 1));
     };
 
-    // producer warp p = warp - 1 stages warp-items q = p, p + 7, ... of a chunk; a warp-item fills
-    // one core matrix (8 rows x 16 bytes) of every plane, lane -> (row % 8, 4-byte column), so the
-    // 32 four-byte stores of a store instruction hit 32 banks
-    //  3xTF32: items 0..63 of A, 64..127 of B^T; item (g, kg): rows g * 8 .., k = kg * 4 + lane / 8
-    //  BF16x3: items 0..31 of A, 32..63 of B^T; item (g, kq): k = 2 (kq * 4 + lane / 8) + {0, 1}
-    // The loads of chunk c + 1 go out right after chunk c is published, so their latency overlaps
-    // the read-back of chunk c - 1 and the MMAs of chunk c.
-    constexpr int NIT = (F == kTF32x3) ? (128 + kProducerWarps - 1) / kProducerWarps
-                                       : (64 + kProducerWarps - 1) / kProducerWarps;
-    float2 v0[NIT], v1[NIT];  // the next chunk's operands (v1: second k of a BF16 pair)
+    // producer warp p = warp - 1 stages warp-items q = p, p + 7, ... of a chunk.  A warp-item is 32
+    // rows x one 16-byte core-matrix column of every plane (4 TF32 or 8 BF16 along k): lane l takes
+    // row 32 rg + l, so each quarter warp writes one whole core matrix (conflict-free 16-byte stores).
+    // Items 0 .. NA - 1 are rows of A (k contiguous in global memory), NA .. 2 NA - 1 rows of B^T
+    // (32 consecutive columns of B per load instruction).  The loads of chunk c + 1 go out right
+    // after chunk c is published, so their latency overlaps the read-back of chunk c - 1 and the
+    // MMAs of chunk c.
+    constexpr int VPL = 16 / Fmt<F>::ELEM;  // k per core-matrix row
+    constexpr int NKG = KC / VPL;           // core-matrix columns per chunk
+    constexpr int NA = 4 * NKG, NITEM = 2 * NA;
+    constexpr int NIT = (NITEM + kProducerWarps - 1) / kProducerWarps;
+    float2 v[NIT][VPL];  // the next chunk's operands
     auto load = [&](int c) {
         const int p = warp - 1, k0 = c * KC;
 #pragma unroll
         for (int i = 0; i < NIT; ++i) {
             const int q = p + kProducerWarps * i;
-            if constexpr (F == kTF32x3) {
-                const int qq = q & 63, g = qq >> 2, kg = qq & 3;
-                const int r = g * 8 + (lane & 7), kk = kg * 4 + (lane >> 3);
-                if (q < 128) v0[i] = (q < 64) ? __ldcg(A + r * 128 + k0 + kk) : __ldcg(B + (k0 + kk) * 128 + r);
-            } else {
-                const int qq = q & 31, g = qq >> 1, kq = qq & 1;
-                const int r = g * 8 + (lane & 7), kk = 2 * (kq * 4 + (lane >> 3));
-                if (q < 32) {
-                    const float4 av = __ldcg(reinterpret_cast<const float4 *>(A + r * 128 + k0 + kk));
-                    v0[i] = make_float2(av.x, av.y);
-                    v1[i] = make_float2(av.z, av.w);
-                } else if (q < 64) {
-                    v0[i] = __ldcg(B + (k0 + kk) * 128 + r);
-                    v1[i] = __ldcg(B + (k0 + kk + 1) * 128 + r);
+            const int qa = q % NA, r = (qa / NKG) * 32 + lane, kk = k0 + (qa % NKG) * VPL;
+            if (q < NA) {
+                // written by this block before its last barrier: plain (coherent) loads
+                const float4 *src = reinterpret_cast<const float4 *>(A + r * 128 + kk);
+#pragma unroll
+                for (int h = 0; h < VPL / 2; ++h) {
+                    const float4 a = src[h];
+                    v[i][2 * h] = make_float2(a.x, a.y);
+                    v[i][2 * h + 1] = make_float2(a.z, a.w);
                 }
+            } else if (q < NITEM) {
+#pragma unroll
+                for (int t = 0; t < VPL; ++t) v[i][t] = __ldcg(B + (kk + t) * 128 + r);
             }
         }
     };
@@ -314,19 +337,21 @@ static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const 
 #pragma unroll
         for (int i = 0; i < NIT; ++i) {
             const int q = p + kProducerWarps * i;
+            const int qa = q % NA;
+            const int o = ((qa / NKG) * 4 + (lane >> 3)) * SBO + (qa % NKG) * kLBO + (lane & 7) * 16;
             if constexpr (F == kTF32x3) {
-                const int qq = q & 63, g = qq >> 2, kg = qq & 3;
-                const int o = g * SBO + kg * kLBO + (lane & 7) * 16 + (lane >> 3) * 4;
-                if (q < 128) put_split(st + (q < 64 ? 0 : 4 * P), o, v0[i]);
+                if (q < NA) put_split<P, 2 * P, 3 * P>(st, o, v[i]);                    // A: Re hi, Re lo, Im hi, Im lo
+                else if (q < NITEM) put_split<2 * P, P, 3 * P>(st + 4 * P, o, v[i]);  // B: Re hi, Im hi, Re lo, Im lo
             } else {
-                const int qq = q & 31, g = qq >> 1, kq = qq & 1;
-                const int o = g * SBO + kq * kLBO + (lane & 7) * 16 + (lane >> 3) * 4;
-                if (q < 64) put_split3(st + (q < 32 ? 0 : 6 * P), o, v0[i], v1[i]);
+                if (q < NA) put_split3<P, 3 * P, P>(st, o, v[i]);                       // A: Re b0..b2, Im b0..b2
+                else if (q < NITEM) put_split3<2 * P, P, 2 * P>(st + 6 * P, o, v[i]);   // B: Re b_t, Im b_t pairs
             }
         }
     };
 
-    // thread 0: the MMAs of chunk c into accumulator set c % 2
+    // thread 0: the MMAs of chunk c into accumulator set c % 2.  The B planes of a term hold Re and
+    // Im back to back (256 rows), so one N = 256 MMA of a Re A term adds Re A Re B into the Re
+    // columns and Re A Im B into the Im columns of the set; the Im A terms take two N = 128 MMAs.
     auto issue = [&](int c) {
         const int s = c % kStages;
         const uint32_t sb = smem_u32(stages + (size_t)s * kStageBytes);
@@ -337,42 +362,37 @@ static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const 
                 const uint32_t o = (uint32_t)ks * 2 * kLBO;
                 const uint64_t arh = desc<F>(sb + o), arl = desc<F>(sb + P + o);
                 const uint64_t aih = desc<F>(sb + 2 * P + o), ail = desc<F>(sb + 3 * P + o);
-                const uint64_t brh = desc<F>(sb + 4 * P + o), brl = desc<F>(sb + 5 * P + o);
-                const uint64_t bih = desc<F>(sb + 6 * P + o), bil = desc<F>(sb + 7 * P + o);
+                const uint64_t brh = desc<F>(sb + 4 * P + o), bih = desc<F>(sb + 5 * P + o);  // [Re; Im] hi
+                const uint64_t brl = desc<F>(sb + 6 * P + o), bil = desc<F>(sb + 7 * P + o);  // [Re; Im] lo
                 const uint32_t acc = ks > 0 ? 1u : 0u;  // fresh accumulator for every chunk
-                // small terms first: Re += Re A Re B - Im A Im B
-                mma<F>(dr, arl, brh, ID, acc);
-                mma<F>(dr, arh, brl, ID, 1u);
-                mma<F>(dr, arh, brh, ID, 1u);
+                // small terms first: [Re | Im] += Re A [Re B | Im B]
+                mma<F>(dr, arl, brh, ID2, acc);
+                mma<F>(dr, arh, brl, ID2, 1u);
+                mma<F>(dr, arh, brh, ID2, 1u);
+                // Re -= Im A Im B, Im += Im A Re B
                 mma<F>(dr, ail, bih, IDN, 1u);
                 mma<F>(dr, aih, bil, IDN, 1u);
                 mma<F>(dr, aih, bih, IDN, 1u);
-                // Im += Re A Im B + Im A Re B
-                mma<F>(di, arl, bih, ID, acc);
-                mma<F>(di, arh, bil, ID, 1u);
-                mma<F>(di, arh, bih, ID, 1u);
                 mma<F>(di, ail, brh, ID, 1u);
                 mma<F>(di, aih, brl, ID, 1u);
                 mma<F>(di, aih, brh, ID, 1u);
             }
         } else {
-            // one K = 16 step; planes: A Re b0..b2, A Im b0..b2, B Re b0..b2, B Im b0..b2
+            // one K = 16 step; planes: A Re b0..b2, A Im b0..b2, then B Re b_t, Im b_t for t = 0..2
             uint64_t ar[3], ai[3], br[3], bi[3];
 #pragma unroll
             for (int t = 0; t < 3; ++t) {
                 ar[t] = desc<F>(sb + t * P);
                 ai[t] = desc<F>(sb + (3 + t) * P);
-                br[t] = desc<F>(sb + (6 + t) * P);
-                bi[t] = desc<F>(sb + (9 + t) * P);
+                br[t] = desc<F>(sb + (6 + 2 * t) * P);
+                bi[t] = desc<F>(sb + (7 + 2 * t) * P);
             }
             // the six terms x_t y_u with t + u <= 2, small first
             constexpr int TT[6] = {2, 1, 0, 1, 0, 0}, UU[6] = {0, 1, 2, 0, 1, 0};
 #pragma unroll
-            for (int w = 0; w < 6; ++w) mma<F>(dr, ar[TT[w]], br[UU[w]], ID, w > 0 ? 1u : 0u);
+            for (int w = 0; w < 6; ++w) mma<F>(dr, ar[TT[w]], br[UU[w]], ID2, w > 0 ? 1u : 0u);
 #pragma unroll
             for (int w = 0; w < 6; ++w) mma<F>(dr, ai[TT[w]], bi[UU[w]], IDN, 1u);
-#pragma unroll
-            for (int w = 0; w < 6; ++w) mma<F>(di, ar[TT[w]], bi[UU[w]], ID, w > 0 ? 1u : 0u);
 #pragma unroll
             for (int w = 0; w < 6; ++w) mma<F>(di, ai[TT[w]], br[UU[w]], ID, 1u);
         }
