@@ -431,9 +431,23 @@ static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const 
     cx.cnt[kBarFree] += NCH / 2;
     cx.cnt[kBarFree + 1] += NCH / 2;
     if (!__syncthreads_or(*(volatile int *)cx.abort)) {
-        float4 *dst = reinterpret_cast<float4 *>(Cout + row * 128 + col0);
+        // C goes out through the idle operand stages (every MMA of the product has completed):
+        // each thread writes its 64 columns of its row there (rows padded to kCRow bytes, so a
+        // quarter warp's 16-byte stores hit distinct banks), then each warp copies whole rows to
+        // global memory with coalesced 512-byte stores (storing each thread's row directly means
+        // 16-byte stores 1 KB apart across a warp, several times slower)
+        constexpr int kCRow = 128 * 8 + 16;
+        static_assert(128 * kCRow <= (int)kSmemBytes, "C fits in the operand stages");
+        float4 *crow = reinterpret_cast<float4 *>(stages + row * kCRow + col0 * 8);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) dst[j] = make_float4(sre[2 * j], sim[2 * j], sre[2 * j + 1], sim[2 * j + 1]);
+        for (int j = 0; j < 32; ++j) crow[j] = make_float4(sre[2 * j], sim[2 * j], sre[2 * j + 1], sim[2 * j + 1]);
+        __syncthreads();
+        for (int r = warp; r < 128; r += 8) {
+            const float4 *src = reinterpret_cast<const float4 *>(stages + r * kCRow);
+            float4 *dst = reinterpret_cast<float4 *>(Cout + r * 128);
+            dst[lane] = src[lane];
+            dst[lane + 32] = src[lane + 32];
+        }
     }
     __syncthreads();
 }
