@@ -114,6 +114,30 @@ def test_batched_workload_sample_and_autotune(prop):
         assert err <= 2 * tol32(p.dim, p.n_steps), (p.name, err)
 
 
+def test_batched_workload_full_size(prop):
+    """All 256 instances of the batched sweep in the benchmark's configuration (autotuned, one FP32
+    launch, graph): every U(T) is unitary within the FP32 bound of its instance, and the two
+    shortest instances of each dimension match the oracle."""
+    import torch
+
+    probs = wl.batched_instances()
+    inst, keep, outs = prop.batch([(p.H0, p.Hk, p.c, p.dt, p.n_steps) for p in probs], "fp32")
+    prop.batch_autotune(inst, "fp32")
+    prop.propagate_batched(inst, "fp32")
+    torch.cuda.synchronize()
+    Us = [U.cpu().numpy().astype(np.complex128) for U in outs]
+    for p, U in zip(probs, Us):
+        unit = np.max(np.abs(U.conj().T @ U - np.eye(p.dim)))
+        assert unit <= tol32(p.dim, p.n_steps), (p.name, unit)
+    picked = []
+    for d in sorted({p.dim for p in probs}):
+        same = sorted((i for i, p in enumerate(probs) if p.dim == d), key=lambda i: probs[i].n_steps)
+        picked += same[:2]
+    for i, r in zip(picked, refs([probs[i] for i in picked], rounded=True)):
+        err = np.max(np.abs(Us[i] - r))
+        assert err <= 2 * tol32(probs[i].dim, probs[i].n_steps), (probs[i].name, err)
+
+
 def test_batched_rejects_host_pointers(prop):
     from paper_2108_07126_gb300 import binding as b
 

@@ -341,6 +341,26 @@ def test_coupled_spins_slice_of_run(prop):
     assert np.max(np.abs(U32 - ref32(full))) <= tol32(16, full.n_steps)
 
 
+def test_dense_stress_full_size(prop, torch):
+    """d = 128 dense stress at N = 2^16 in the benchmark's launch configuration: FP32, 3xTF32 and
+    split BF16x3 stay unitary and agree with the FP64 path within the FP32 bound; the FP64 path
+    is unitary; every precision matches the oracle on a 2^9-slice instance of the workload."""
+    prob = wl.dense_stress()
+    N, I = prob.n_steps, np.eye(128)
+    U64 = run(prop, prob, "fp64")
+    assert np.max(np.abs(U64.conj().T @ U64 - I)) <= 1e-10
+    f32 = dict(c_dtype=torch.float32, h_dtype=torch.complex64)
+    for prec in ("fp32", "fp32_tc_tf32x3", "fp32_tc_bf16x3"):
+        U = run(prop, prob, prec, **f32)
+        unit, err = np.max(np.abs(U.conj().T @ U - I)), np.max(np.abs(U - U64))
+        print(f"{prec}: unitarity {unit:.2e}  vs FP64 {err:.2e}  bound {tol32(128, N):.2e}")
+        assert unit <= tol32(128, N) and err <= 2 * tol32(128, N)
+    head = wl.dense_stress(n_steps=1 << 9)
+    R = ref32(head)
+    for prec in ("fp32", "fp32_tc_tf32x3", "fp32_tc_bf16x3"):
+        assert np.max(np.abs(run(prop, head, prec, **f32) - R)) <= 2 * tol32(128, head.n_steps)
+
+
 def test_fp32_unitary_step_removes_coherent_drift(prop):
     """Coupled spins, 2^18 slices: repeated FP32 rounding drifts U off the unitary group; one
     Newton-Schulz step per leaf product (the default) keeps it unitary and closer to the oracle."""
