@@ -433,19 +433,36 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
         const Real sc = pow2neg<Real>(s);
         Real *gpk = (TCM >= 2) ? (Real *)panels : (Real *)P0;  // resident: the free slot P0 in shared memory
 
-        // packed exponent sum_b gamma_b P_b, four entries per thread and step (independent loads)
-        for (int e4 = tid; e4 < DD / 4; e4 += kLargeThreads) {
-            Real v[4] = {Real(0), Real(0), Real(0), Real(0)};
-            for (int b = 0; b < nb; ++b) {
-                Real w[4];
-                ld4<Real>(packed + (size_t)b * DD + 4 * e4, w);
-                const Real g = gam[b];
+        // packed exponent sum_b gamma_b P_b: EP groups of four entries per thread and step, the
+        // basis loop unrolled, so that 4 EP independent 16-byte loads from L2 are in flight (the
+        // basis is read once per slice and does not fit in shared memory)
+        {
+            constexpr int NE4 = DD / 4, EP = (NE4 / kLargeThreads) < 4 ? (NE4 / kLargeThreads) : 4;
+            static_assert(EP >= 1 && NE4 % (EP * kLargeThreads) == 0, "assembly steps cover the matrix");
+            for (int e0 = tid; e0 < NE4; e0 += EP * kLargeThreads) {
+                Real v[EP][4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) v[u] = fma(g, w[u], v[u]);
+                for (int q = 0; q < EP; ++q)
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v[q][u] = Real(0);
+#pragma unroll 4
+                for (int b = 0; b < nb; ++b) {
+                    const Real g = gam[b];
+                    Real w[EP][4];
+#pragma unroll
+                    for (int q = 0; q < EP; ++q) ld4<Real>(packed + (size_t)b * DD + 4 * (e0 + q * kLargeThreads), w[q]);
+#pragma unroll
+                    for (int q = 0; q < EP; ++q)
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) v[q][u] = fma(g, w[q][u], v[q][u]);
+                }
+#pragma unroll
+                for (int q = 0; q < EP; ++q) {
+                    const int e4 = e0 + q * kLargeThreads, i = (4 * e4) / D, jj = (4 * e4) % D;
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) gpk[i * GLD + jj + u] = v[q][u];
+                }
             }
-            const int i = (4 * e4) / D, jj = (4 * e4) % D;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) gpk[i * GLD + jj + u] = v[u];
         }
         __syncthreads();
         // Hermitian unpack (upper triangle: Re, strict lower: Im) into A = -i G / 2^s, or into
