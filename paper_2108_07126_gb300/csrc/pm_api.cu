@@ -68,7 +68,8 @@ namespace {
 constexpr int kMaxDim = 256;
 constexpr int kMaxBatchDim = 128;  // the batched kernel's block-level bodies go up to D = 128
 constexpr int kMaxSmallDim = 16;  // larger dimensions use one thread block per leaf
-constexpr int kLeafMinSteps = 8;  // fewer blocks for short runs: each leaf gets >= 8 slices
+constexpr int kLeafMinSteps = 8;    // fewer blocks for short runs: each leaf gets >= 8 slices (FP32)
+constexpr int kLeafMinSteps64 = 2;  // the same for FP64, whose slices cost far more than the tree
 
 struct Workspace {
     void *ptr = nullptr;
@@ -975,6 +976,17 @@ int forward_setup(parament_ctx *ctx, int fp64, void *U_dst, FusedParams &p, int 
     if (warps <= 0) {
         warps = max_warps;
         while (warps > 1 && fused_smem(Dp, fp64, nb, warps) > ctx->smem_optin) --warps;
+        if (fp64 && ctx->opt_grid <= 0) {
+            // an FP64 slice costs ~64x an FP32 one (GB300's FP64 rate), so a short run is spread
+            // over more SMs first: halve the warps per block while the grid that gives every leaf
+            // kLeafMinSteps64 slices stays below one block per SM (d = 2, N = 2^14: 8 x 256 ->
+            // 128 x 64 threads, 2.2x faster)
+            auto blocks_for = [&](int w) {
+                const int64_t per = (int64_t)w * fused_gpw(Dp, fp64) * kLeafMinSteps64;
+                return (ctx->n_steps + per - 1) / per;
+            };
+            while (warps > 2 && blocks_for(warps) < ctx->sm_count) warps /= 2;
+        }
     }
     if (warps > max_warps) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "at most %d warps per block", max_warps);
     smem = fused_smem(Dp, fp64, nb, warps);
@@ -986,8 +998,8 @@ int forward_setup(parament_ctx *ctx, int fp64, void *U_dst, FusedParams &p, int 
     leaves_per_block = warps * fused_gpw(Dp, fp64);
     grid = (int)ctx->opt_grid;
     if (grid <= 0) {
-        const int64_t need = (ctx->n_steps + (int64_t)leaves_per_block * kLeafMinSteps - 1) /
-                             ((int64_t)leaves_per_block * kLeafMinSteps);
+        const int lm = fp64 ? kLeafMinSteps64 : kLeafMinSteps;
+        const int64_t need = (ctx->n_steps + (int64_t)leaves_per_block * lm - 1) / ((int64_t)leaves_per_block * lm);
         grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)bps * ctx->sm_count));
     }
     grid = std::min(grid, ctx->max_grid);
