@@ -315,8 +315,10 @@ __device__ void cta_mm_tc(const float2 *__restrict__ A, const float2 *__restrict
 template <int D>
 __device__ __forceinline__ void smem_mm(const float2 *__restrict__ A, const float2 *__restrict__ B,
                                         float2 *__restrict__ Cout) {
+    // thread (ty, tx): rows ty + 16 r, column pairs 32 p + 2 tx (p < TC / 2), so the 16-byte B loads
+    // and C stores of a quarter warp cover 128 contiguous bytes
     constexpr int TR = D / 16, TC = D / 16;
-    static_assert(TR * TC * kLargeThreads == D * D && TC % 2 == 0, "thread tiling");
+    static_assert(TR * TC * kLargeThreads == D * D && TC % 2 == 0 && 16 * TC == D, "thread tiling");
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
     float2 acc[TR][TC];
 #pragma unroll
@@ -336,7 +338,7 @@ __device__ __forceinline__ void smem_mm(const float2 *__restrict__ A, const floa
         for (int u = 0; u < 2; ++u)
 #pragma unroll
             for (int c = 0; c < TC; c += 2) {
-                const float4 v = *reinterpret_cast<const float4 *>(B + (k + u) * D + TC * tx + c);
+                const float4 v = *reinterpret_cast<const float4 *>(B + (k + u) * D + 16 * c + 2 * tx);
                 b[u][c] = make_float2(v.x, v.y);
                 b[u][c + 1] = make_float2(v.z, v.w);
             }
@@ -351,7 +353,7 @@ __device__ __forceinline__ void smem_mm(const float2 *__restrict__ A, const floa
     for (int r = 0; r < TR; ++r)
 #pragma unroll
         for (int c = 0; c < TC; c += 2)
-            *reinterpret_cast<float4 *>(Cout + (ty + 16 * r) * D + TC * tx + c) =
+            *reinterpret_cast<float4 *>(Cout + (ty + 16 * r) * D + 16 * c + 2 * tx) =
                 make_float4(acc[r][c].x, acc[r][c].y, acc[r][c + 1].x, acc[r][c + 1].y);
     __syncthreads();
 }
