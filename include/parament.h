@@ -129,7 +129,7 @@ typedef enum {
     PARAMENT_OPT_WORKSPACE_MB = 9,
     /* batched: target slices per leaf (0 = default 64) */
     PARAMENT_OPT_BATCH_LEAF_STEPS = 10,
-    /* batched: work items per SM (0 = default 4) */
+    /* batched: work items per SM (0 = default 32) */
     PARAMENT_OPT_BATCH_ITEMS_PER_SM = 11,
     /* batched: 1 (default) = capture set-up and launch in a CUDA graph and replay it; 0 = launch directly */
     PARAMENT_OPT_BATCH_GRAPH = 12,
@@ -298,8 +298,8 @@ int parament_propagate_batched(parament_ctx *ctx, const parament_instance *inst,
 
 /*
  * Autotuner of the batched launch: times the batch for every pair of
- * (target slices per leaf in {32, 64, 128, 256}) x (work items per SM in
- * {2, 4, 8}), keeps the fastest in the context options
+ * (target slices per leaf in {32, 128}) x (work items per SM in
+ * {8, 16, 32, 64}), keeps the fastest in the context options
  * PARAMENT_OPT_BATCH_LEAF_STEPS / PARAMENT_OPT_BATCH_ITEMS_PER_SM and reports
  * it (and its time in ms) through the optional outputs.  Waits for the GPU.
  */

@@ -1615,7 +1615,7 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
             return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "instance %d: batched calls take device pointers", i);
     }
     const int leaf_steps = ctx->opt_batch_leaf > 0 ? (int)ctx->opt_batch_leaf : 64;
-    const int items_per_sm = ctx->opt_batch_items > 0 ? (int)ctx->opt_batch_items : 4;
+    const int items_per_sm = ctx->opt_batch_items > 0 ? (int)ctx->opt_batch_items : 32;
     const size_t csz = fp64 ? 16 : 8, rsz = fp64 ? 8 : 4;
 
     std::vector<int64_t> key = {n, dtype, cdtype, integ, prec, leaf_steps, items_per_sm};
@@ -1854,12 +1854,12 @@ int parament_batch_autotune(parament_ctx *ctx, const parament_instance *inst, in
     if (!ctx) return PARAMENT_ERR_INVALID_VALUE;
     ctx->err.clear();
     DeviceGuard guard(ctx->device);
-    const int leafs[] = {32, 64, 128, 256}, items[] = {2, 4, 8};
+    const int leafs[] = {32, 128}, items[] = {8, 16, 32, 64};
     cudaEvent_t a, b;
     PM_CUDA(cudaEventCreate(&a));
     PM_CUDA(cudaEventCreate(&b));
     double best = 1e300;
-    int bl = 64, bi = 4;
+    int bl = 128, bi = 32;
     int st = PARAMENT_OK;
     for (int l : leafs) {
         for (int it : items) {

@@ -97,11 +97,25 @@ __global__ void batch_basis_kernel(const BatchInst *insts, const int2 *table, in
     }
 }
 
+// The bodies run as separate (not inlined) functions: each keeps its own register allocation.
+// Inlined into one switch they shared 255 registers and spilled 1.3 KB per thread, and the
+// d = 64 items (most of the work of a mixed sweep) ran 1.5x slower than as single problems.
+template <typename Real, int D, int INTEG>
+static __device__ __noinline__ void batch_fused_item(const FusedParams &p, int blk, int nblk, unsigned char *smem) {
+    fused_body<Real, D, INTEG>(p, blk, nblk, smem);
+}
+
+template <typename Real, int D, int INTEG, int TCM>
+static __device__ __noinline__ void batch_large_item(const FusedParams &p, unsigned char *ws, int blk, int nblk,
+                                                     unsigned char *smem) {
+    large_body<Real, D, INTEG, TCM>(p, (typename Cx<Real>::T *)ws, blk, nblk, smem);
+    large_arrival_tree<Real, D>(p, ws, blk, nblk, smem);
+}
+
 template <typename Real, int INTEG, bool TC>
 __global__ void __launch_bounds__(256, 1) batched_kernel(const BatchItem *__restrict__ items, int n_items,
                                                          unsigned *queue, const FusedParams *__restrict__ params,
                                                          unsigned char *scratch, size_t scratch_stride) {
-    using C = typename Cx<Real>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
     unsigned char *ws = scratch + (size_t)blockIdx.x * scratch_stride;
@@ -114,22 +128,14 @@ __global__ void __launch_bounds__(256, 1) batched_kernel(const BatchItem *__rest
         const BatchItem w = items[it];
         const FusedParams &p = params[w.inst];
         switch (w.Dp) {
-            case 2: fused_body<Real, 2, INTEG>(p, w.blk, w.nblk, smem); break;
-            case 4: fused_body<Real, 4, INTEG>(p, w.blk, w.nblk, smem); break;
-            case 8: fused_body<Real, 8, INTEG>(p, w.blk, w.nblk, smem); break;
-            case 16: fused_body<Real, 16, INTEG>(p, w.blk, w.nblk, smem); break;
-            case 32:
-                large_body<Real, 32, INTEG, 0>(p, (C *)ws, w.blk, w.nblk, smem);  // faster than 3xTF32 here
-                large_arrival_tree<32>(p, ws, w.blk, w.nblk, smem);
-                break;
-            case 64:
-                large_body<Real, 64, INTEG, 0>(p, (C *)ws, w.blk, w.nblk, smem);  // faster than 3xTF32 here
-                large_arrival_tree<64>(p, ws, w.blk, w.nblk, smem);
-                break;
-            case 128:
-                large_body<Real, 128, INTEG, TC ? 1 : 0>(p, (C *)ws, w.blk, w.nblk, smem);
-                large_arrival_tree<128>(p, ws, w.blk, w.nblk, smem);
-                break;
+            case 2: batch_fused_item<Real, 2, INTEG>(p, w.blk, w.nblk, smem); break;
+            case 4: batch_fused_item<Real, 4, INTEG>(p, w.blk, w.nblk, smem); break;
+            case 8: batch_fused_item<Real, 8, INTEG>(p, w.blk, w.nblk, smem); break;
+            case 16: batch_fused_item<Real, 16, INTEG>(p, w.blk, w.nblk, smem); break;
+            // CUDA-core products at 32 and 64 (faster than 3xTF32 there)
+            case 32: batch_large_item<Real, 32, INTEG, 0>(p, ws, w.blk, w.nblk, smem); break;
+            case 64: batch_large_item<Real, 64, INTEG, 0>(p, ws, w.blk, w.nblk, smem); break;
+            case 128: batch_large_item<Real, 128, INTEG, TC ? 1 : 0>(p, ws, w.blk, w.nblk, smem); break;
         }
         __syncthreads();
     }

@@ -692,10 +692,13 @@ __global__ void __launch_bounds__(kLargeThreads, 1) large_kernel(const FusedPara
 }
 
 // Pairwise tree over the nblk leaf products of one problem without waiting:
-// the second block to reach a node multiplies (later on the left, FP64 products
-// through the block's scratch), the first one leaves; the root writes U_out and
-// snapshots the statistics.
-template <int D>
+// the second block to reach a node multiplies (later on the left, through the
+// block's scratch), the first one leaves; the root writes U_out and snapshots
+// the statistics.  As in the single-problem tree, the levels with at most 8
+// nodes multiply in FP64 and the levels below in Real (the partials stay FP64
+// in global memory): an FP64 product of two 64 x 64 matrices costs an SM
+// ~0.5 M cycles on GB300's FP64 pipe, as much as the FP32 work of ~5 slices.
+template <typename Real, int D>
 __device__ void large_arrival_tree(const FusedParams &p, void *ws_bytes, int blk, int nblk, unsigned char *smem) {
     constexpr int DD = D * D;
     __shared__ int s_second;
@@ -712,12 +715,24 @@ __device__ void large_arrival_tree(const FusedParams &p, void *ws_bytes, int blk
             __threadfence();
             double2 *gL = p.partials + (size_t)((idx & ~1) << level) * DD;
             const double2 *gR = p.partials + (size_t)((idx | 1) << level) * DD;
-            for (int e = tid; e < DD; e += kLargeThreads) {
-                L2[e] = __ldcg(gL + e);
-                R2[e] = __ldcg(gR + e);
+            if (std::is_same<Real, double>::value || n <= 8) {
+                for (int e = tid; e < DD; e += kLargeThreads) {
+                    L2[e] = __ldcg(gL + e);
+                    R2[e] = __ldcg(gR + e);
+                }
+                __syncthreads();
+                cta_mm<double, D>(R2, L2, gL, smem);
+            } else {
+                float2 *Lf = (float2 *)ws_bytes, *Rf = Lf + DD, *Cf = Rf + DD;
+                for (int e = tid; e < DD; e += kLargeThreads) {
+                    const double2 l = __ldcg(gL + e), r = __ldcg(gR + e);
+                    Lf[e] = make_float2((float)l.x, (float)l.y);
+                    Rf[e] = make_float2((float)r.x, (float)r.y);
+                }
+                __syncthreads();
+                cta_mm<float, D>(Rf, Lf, Cf, smem);
+                for (int e = tid; e < DD; e += kLargeThreads) gL[e] = make_double2((double)Cf[e].x, (double)Cf[e].y);
             }
-            __syncthreads();
-            cta_mm<double, D>(R2, L2, gL, smem);
             __threadfence();
             __syncthreads();
         }
