@@ -205,7 +205,10 @@ int parament_set_hamiltonians(parament_ctx *ctx, int dim, int n_ctrl, const void
  * slices of duration dt (Sec. 3.2: amplitudes sampled at equidistant times;
  * S per integrator as documented above).  A device pointer is borrowed, not
  * copied: it must stay valid and unchanged until the propagations that use
- * it have run on the stream.  Host data is copied into a context buffer.
+ * it have run on the stream.  Page-locked (pinned) host memory is borrowed the
+ * same way: the kernels read it in place over the host link, so the transfer
+ * overlaps the computation.  Other host data is copied into a context buffer
+ * (asynchronously on the context's stream).
  * 0 <= n_steps < 2^31 (0 gives U = I), dt finite.  Requires set_hamiltonians.
  */
 int parament_set_controls(parament_ctx *ctx, const void *c, parament_real_dtype cdtype, int64_t n_steps,

@@ -186,6 +186,18 @@ void ws_free(Workspace &w) {
     w.bytes = 0;
 }
 
+// Device address of page-locked host memory (readable by the kernels in place over the host
+// link), or null for any other pointer.
+const void *pinned_device_ptr(const void *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 bool is_device_ptr(const void *p) {
     if (!p) return false;
     cudaPointerAttributes a;
@@ -908,10 +920,16 @@ int parament_set_controls(parament_ctx *ctx, const void *c, parament_real_dtype 
     DeviceGuard guard(ctx->device);
     const void *use = c;
     if (bytes > 0 && !is_device_ptr(c)) {
-        int st = ws_reserve(ctx, ctx->ctrl_copy, bytes);
-        if (st) return st;
-        PM_CUDA(cudaMemcpyAsync(ctx->ctrl_copy.ptr, c, bytes, cudaMemcpyHostToDevice, ctx->stream));
-        use = ctx->ctrl_copy.ptr;
+        if (const void *mapped = pinned_device_ptr(c)) {
+            // page-locked host memory: the kernels read the samples in place, so the transfer
+            // overlaps the computation instead of preceding it (each sample is read once)
+            use = mapped;
+        } else {
+            int st = ws_reserve(ctx, ctx->ctrl_copy, bytes);
+            if (st) return st;
+            PM_CUDA(cudaMemcpyAsync(ctx->ctrl_copy.ptr, c, bytes, cudaMemcpyHostToDevice, ctx->stream));
+            use = ctx->ctrl_copy.ptr;
+        }
     }
     if (bytes > 0 && ((uintptr_t)use % esz))
         return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "control pointer not aligned to its element size");

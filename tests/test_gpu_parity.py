@@ -341,6 +341,28 @@ def test_coupled_spins_slice_of_run(prop):
     assert np.max(np.abs(U32 - ref32(full))) <= tol32(16, full.n_steps)
 
 
+@pytest.mark.parametrize("d", [8, 40])
+def test_host_controls_pinned_and_pageable(prop, torch, d):
+    """Controls in page-locked host memory are read by the kernels in place, pageable host
+    controls are copied first: both give bit-for-bit the U(T) of device-resident controls, and
+    a host U_out receives it."""
+    from paper_2108_07126_gb300 import binding as b
+
+    prob = wl.random_problem(d, 3, 3000 if d <= 16 else 200, "magnus4_gl2", seed=4242 + d, g_norm=0.4)
+    prop.set_hamiltonians(torch.as_tensor(prob.H0).to(torch.complex64), torch.as_tensor(prob.Hk).to(torch.complex64),
+                          prob.integrator)
+    c32 = torch.as_tensor(prob.c).to(torch.float32)
+    prop.set_controls(c32.cuda(), prob.dt, prob.n_steps)
+    U_dev = prop.propagate("fp32").cpu().numpy()
+    pinned = c32.pin_memory()
+    pageable = np.ascontiguousarray(c32.numpy())
+    for ptr in (pinned.data_ptr(), pageable.ctypes.data):
+        U_host = np.zeros((d, d), np.complex64)
+        b.parament_set_controls(prop.ctx, ptr, b.PARAMENT_F32, prob.n_steps, prob.dt)
+        b.parament_propagate(prop.ctx, U_host.ctypes.data, b.PARAMENT_PREC_FP32)
+        assert np.array_equal(U_host, U_dev)
+
+
 def test_dense_stress_full_size(prop, torch):
     """d = 128 dense stress at N = 2^16 in the benchmark's launch configuration: FP32, 3xTF32 and
     split BF16x3 stay unitary and agree with the FP64 path within the FP32 bound; the FP64 path
