@@ -107,3 +107,21 @@ def test_reference_arm_json_contract():
     assert d["config"]["workload"].startswith("coupled_spins_d16") and d["config"]["n_steps"] == 1 << 20
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["cores"] >= 1
+
+
+def test_parallel_oracle_timing_matches_the_oracle():
+    """The CPU baseline cuts the sample into contiguous slice ranges run by separate oracle
+    processes; the ordered product of their partial products is the oracle's U."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_2108_07126_gb300 import workloads as wl
+
+    n = 600
+    o = bench.time_oracle(n, workers=4)
+    prob = wl.coupled_spins(n_steps=n)
+    R = oracle.propagate(prob.H0, prob.Hk, prob.c, prob.dt, prob.integrator)
+    assert o["cores"] == 4 and o["n"] == n and o["seconds"] > 0 and o["one_core_rate"] > 0
+    assert np.max(np.abs(o["U"] - R)) <= 1e-12
