@@ -192,3 +192,24 @@ def test_autograd_function(prop):
     l_ref, g_ref, _ = oracle.loss_and_gradient(prob.H0, prob.Hk, prob.c, prob.dt, V)
     assert abs(L.item() - l_ref) <= 1e-11
     assert np.max(np.abs(g.cpu().numpy() - 3.0 * g_ref)) <= 1e-9 * 3.0 * np.max(np.abs(g_ref))
+
+
+@pytest.mark.parametrize("integrator", ["midpoint", "magnus4_simpson"])
+def test_gradient_with_pinned_host_controls(prop, integrator):
+    """Controls in page-locked host memory (read by the kernels in place) give bit-for-bit the
+    loss and gradient of device-resident controls."""
+    import torch
+
+    from paper_2108_07126_gb300 import binding as b
+
+    prob = wl.random_problem(4, 2, 700, integrator, seed=5150, g_norm=0.3)
+    V = wl.haar_unitary(np.random.default_rng(5151), 4)
+    prop.set_hamiltonians(torch.as_tensor(prob.H0), torch.as_tensor(prob.Hk), integrator)
+    c = torch.as_tensor(prob.c)
+    prop.set_controls(c.cuda(), prob.dt, prob.n_steps)
+    loss_d, g_d = prop.propagate_grad(V, "fp64")
+    pinned = c.pin_memory()
+    b.parament_set_controls(prop.ctx, pinned.data_ptr(), b.PARAMENT_F64, prob.n_steps, prob.dt)
+    loss_h, g_h = prop.propagate_grad(V, "fp64")
+    torch.cuda.synchronize()
+    assert loss_h == loss_d and torch.equal(g_h, g_d)
