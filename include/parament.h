@@ -160,9 +160,15 @@ typedef struct {
     int64_t exp_products;     /* complex d x d products in exponentials and squarings */
     int64_t tree_products;    /* complex d x d products in the product tree */
     uint32_t device_status;   /* PARAMENT_DEV_* bits raised by the kernels */
-    uint32_t reserved1;
+    uint32_t product_backends; /* PARAMENT_BACKEND_* bits: the code that ran the complex products */
     double kernel_ms;         /* device time of the propagation kernels (events) */
 } parament_stats;
+
+/* product back-ends reported in parament_stats.product_backends (a batched call ORs the
+   back-ends of its dimension classes) */
+#define PARAMENT_BACKEND_CUDA_CORES 0x1u /* FP32 / FP64 fused multiply-adds */
+#define PARAMENT_BACKEND_MMA_SYNC 0x2u   /* warp-level mma.sync TF32 tensor-core instructions */
+#define PARAMENT_BACKEND_TCGEN05 0x4u    /* tcgen05.mma with tensor-memory accumulators */
 
 #define PARAMENT_DEV_NONFINITE_NORM 0x1u /* a slice's norm bound was NaN/Inf */
 #define PARAMENT_DEV_NORM_CAPPED 0x2u    /* a norm exceeded the largest scaling in the table */
@@ -351,11 +357,22 @@ int parament_taylor_choice(double norm_bound, double u, int force_m, int *m_out,
  * which loads the library holds until the process exits.
  *   - H0 (d x d), Hk (K x d x d), c (K x S), U_out (d x d): device pointers,
  *     layouts and S as for the context API; `dtype` for H and U, `cdtype` must
- *     match `prec` (F64 with FP64, F32 with FP32).  The caller owns them all.
+ *     match `prec` (F64 with FP64, F32 with FP32).  U_out must be aligned to
+ *     its element (8 bytes for C64, 16 for C128) and c to its real type.  The
+ *     caller owns them all.
+ *   - device_status: NULL = return without waiting.  Otherwise the call waits
+ *     for its work on the stream and stores there the PARAMENT_DEV_* bits the
+ *     kernel raised (PARAMENT_DEV_NONFINITE_NORM: NaN or Inf reached a norm
+ *     bound, i.e. in H0, Hk or c, and U is not valid; PARAMENT_DEV_NORM_CAPPED:
+ *     a slice needed more squarings than the table holds).  This path does not
+ *     check H or c for NaN / Inf before the launch, so that word is its only
+ *     report of non-finite input.
  *   - Limits: d <= PARAMENT_NOALLOC_MAX_DIM, 1 + K (midpoint) or
  *     1 + K (K + 3) / 2 (Magnus) <= PARAMENT_NOALLOC_MAX_BASIS, at most
- *     PARAMENT_NOALLOC_MAX_BLOCKS thread blocks.  Beyond a limit: UNSUPPORTED;
- *     host pointers, mismatched dtypes, bad sizes: INVALID_VALUE.
+ *     PARAMENT_NOALLOC_MAX_BLOCKS thread blocks (more slices run in longer
+ *     leaves).  Beyond a limit, or a precision other than FP64 / FP32:
+ *     UNSUPPORTED.  Host pointers, misaligned pointers, mismatched or unknown
+ *     dtypes, d < 1, bad sizes: INVALID_VALUE.  Non-finite dt: NONFINITE.
  *   - The first call on a device, with that device current, looks up the
  *     array's device address (cudaGetSymbolAddress); make that first call
  *     before any stream capture.
@@ -374,7 +391,8 @@ int parament_taylor_choice(double norm_bound, double u, int force_m, int *m_out,
 #define PARAMENT_NOALLOC_SCRATCH_BYTES 1641472
 int parament_propagate_noalloc(int dim, int n_ctrl, const void *H0, const void *Hk, parament_dtype dtype,
                                parament_integrator integrator, const void *c, parament_real_dtype cdtype,
-                               int64_t n_steps, double dt, void *U_out, parament_precision prec, void *cuda_stream);
+                               int64_t n_steps, double dt, void *U_out, parament_precision prec, void *cuda_stream,
+                               uint32_t *device_status);
 
 /*
  * Chebyshev exponential (Sec. 2.1): the largest half-width beta of the spectral

@@ -66,6 +66,11 @@ PARAMENT_OPT_UNITARY_STEP = 14
 
 PARAMENT_DEV_NONFINITE_NORM = 0x1
 PARAMENT_DEV_NORM_CAPPED = 0x2
+PARAMENT_DEV_TENSOR_TIMEOUT = 0x4
+
+PARAMENT_BACKEND_CUDA_CORES = 0x1
+PARAMENT_BACKEND_MMA_SYNC = 0x2
+PARAMENT_BACKEND_TCGEN05 = 0x4
 
 INTEGRATORS = {"midpoint": PARAMENT_MIDPOINT, "magnus4_gl2": PARAMENT_MAGNUS4_GL2,
                "magnus4_simpson": PARAMENT_MAGNUS4_SIMPSON}
@@ -87,7 +92,7 @@ class parament_stats(ctypes.Structure):
         ("exp_products", ctypes.c_int64),
         ("tree_products", ctypes.c_int64),
         ("device_status", ctypes.c_uint32),
-        ("reserved1", ctypes.c_uint32),
+        ("product_backends", ctypes.c_uint32),
         ("kernel_ms", ctypes.c_double),
     ]
 
@@ -127,8 +132,8 @@ _SIGS = {
     "parament_taylor_choice": ([ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                 ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "parament_propagate_noalloc": ([ctypes.c_int, ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int, _vp,
-                                    ctypes.c_int, ctypes.c_int64, ctypes.c_double, _vp, ctypes.c_int, _vp],
-                                   ctypes.c_int),
+                                    ctypes.c_int, ctypes.c_int64, ctypes.c_double, _vp, ctypes.c_int, _vp,
+                                    ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "parament_propagate_batched": ([_vp, ctypes.POINTER(parament_instance), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "parament_batch_autotune": ([_vp, ctypes.POINTER(parament_instance), ctypes.c_int, ctypes.c_int, ctypes.c_int,
@@ -240,11 +245,17 @@ def parament_taylor_choice(norm_bound: float, u: float, force_m: int = 0) -> tup
 
 def parament_propagate_noalloc(dim: int, n_ctrl: int, H0_ptr: int, Hk_ptr: int | None, dtype: int, integrator: int,
                                c_ptr: int | None, cdtype: int, n_steps: int, dt: float, U_ptr: int, prec: int,
-                               stream: int | None = None) -> None:
-    """One propagation that allocates nothing (device pointers only; see parament.h)."""
+                               stream: int | None = None, wait_status: bool = False) -> int | None:
+    """One propagation that allocates nothing (device pointers only; see parament.h).
+
+    With ``wait_status`` the call waits and returns the PARAMENT_DEV_* bits of the kernel.
+    """
+    st = ctypes.c_uint32(0)
     _check(_lib.parament_propagate_noalloc(int(dim), int(n_ctrl), H0_ptr, Hk_ptr or None, int(dtype),
                                            int(integrator), c_ptr or None, int(cdtype), int(n_steps), float(dt),
-                                           U_ptr, int(prec), stream or None))
+                                           U_ptr, int(prec), stream or None,
+                                           ctypes.byref(st) if wait_status else None))
+    return st.value if wait_status else None
 
 
 def _instances(inst):

@@ -630,6 +630,23 @@ int large_blocks_per_sm(int Dp, int fp64, int integ, size_t smem, int tc) {
     return memo_occupancy(1, Dp, fp64, integ, 8, smem, tc,
                           [&] { return large_blocks_per_sm_uncached(Dp, fp64, integ, smem, tc); });
 }
+// the code that runs the complex products of parament_propagate for one padded dimension and
+// precision (tc: 0 none, 1 3xTF32, 2 split BF16x3), as PARAMENT_BACKEND_* bits
+template <int D>
+unsigned large_backend_bits(int tc) {
+    const int tcm = tc == 1 ? large_tcm<float, D, 1>() : large_tcm<float, D, 2>();
+    return tcm == 0 ? PARAMENT_BACKEND_CUDA_CORES : (tcm == 1 ? PARAMENT_BACKEND_MMA_SYNC : PARAMENT_BACKEND_TCGEN05);
+}
+unsigned product_backend(int Dp, int fp64, int tc) {
+    if (Dp <= kMaxSmallDim || fp64 || tc == 0) return PARAMENT_BACKEND_CUDA_CORES;
+    switch (Dp) {
+        case 32: return large_backend_bits<32>(tc);
+        case 64: return large_backend_bits<64>(tc);
+        case 128: return large_backend_bits<128>(tc);
+        case 256: return large_backend_bits<256>(tc);
+    }
+    return PARAMENT_BACKEND_CUDA_CORES;
+}
 size_t large_smem(int Dp, int fp64, int nb, int tc = 0) {
     switch (Dp) {
         case 32: return large_smem_d32(fp64, nb, tc);
@@ -1052,7 +1069,8 @@ cudaError_t forward_launch(parament_ctx *ctx, int fp64, const FusedParams &p, in
     return fused_dispatch(ctx->dpad, fp64, (int)ctx->integ, p, grid, warps, smem, ctx->stream);
 }
 
-void record_launch(parament_ctx *ctx, int nb, int grid, int warps, int leaves_per_block) {
+void record_launch(parament_ctx *ctx, int nb, int grid, int warps, int leaves_per_block,
+                   unsigned backends = PARAMENT_BACKEND_CUDA_CORES) {
     ctx->last = parament_stats{};
     ctx->last.n_steps = ctx->n_steps;
     ctx->last.dim = ctx->dim;
@@ -1060,6 +1078,7 @@ void record_launch(parament_ctx *ctx, int nb, int grid, int warps, int leaves_pe
     ctx->last.grid_blocks = grid;
     ctx->last.block_threads = warps * 32;
     ctx->last.leaves = grid * leaves_per_block;
+    ctx->last.product_backends = backends;
     ctx->last.kernel_ms = -1.0;
 }
 
@@ -1159,7 +1178,7 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) 
     } else {
         PM_CUDA(forward_launch(ctx, fp64, p, grid, warps, smem, tc));
     }
-    record_launch(ctx, ctx->nb_eff, grid, warps, lpb);
+    record_launch(ctx, ctx->nb_eff, grid, warps, lpb, product_backend(ctx->dpad, fp64, tc));
 
     if (host_out) {
         PM_CUDA(cudaMemcpyAsync(U_out, dst, (size_t)ctx->dim * ctx->dim * esz, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1603,6 +1622,12 @@ int batched_occupancy(int variant, size_t smem) {
     return 0;
 }
 
+// the code that runs the complex products of one dimension class of the batched kernel
+unsigned batch_backend(int Dp, int fp64, int tc) {
+    if (fp64 || !tc || Dp <= 64) return PARAMENT_BACKEND_CUDA_CORES;
+    return PARAMENT_BACKEND_MMA_SYNC;
+}
+
 // Build (when the shapes change) and enqueue one batched propagation.
 int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_dtype dtype,
               parament_real_dtype cdtype, parament_integrator integ, parament_precision prec) {
@@ -1844,9 +1869,14 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
         PM_CUDA(enqueue());
     }
     int64_t tot = 0;
-    for (int i = 0; i < n; ++i) tot += inst[i].n_steps;
+    unsigned backends = 0;
+    for (int i = 0; i < n; ++i) {
+        tot += inst[i].n_steps;
+        backends |= batch_backend(pad_dim(inst[i].dim), fp64, tc);
+    }
     ctx->last = parament_stats{};
     ctx->last.n_steps = tot;
+    ctx->last.product_backends = backends;
     ctx->last.grid_blocks = ctx->b_grid;
     ctx->last.block_threads = 256;
     ctx->last.leaves = ctx->b_n_items;

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 #include <mutex>
 
@@ -79,16 +80,19 @@ bool on_device(const void *p) {
 extern "C" int parament_propagate_noalloc(int dim, int n_ctrl, const void *H0, const void *Hk, parament_dtype dtype,
                                           parament_integrator integrator, const void *c,
                                           parament_real_dtype cdtype, int64_t n_steps, double dt, void *U_out,
-                                          parament_precision prec, void *cuda_stream) {
-    if (dim < 1 || dim > kNaMaxDim || n_ctrl < 0 || n_ctrl > pm::kMaxControls) return PARAMENT_ERR_INVALID_VALUE;
+                                          parament_precision prec, void *cuda_stream, uint32_t *device_status) {
+    if (dim < 1 || n_ctrl < 0 || n_ctrl > pm::kMaxControls) return PARAMENT_ERR_INVALID_VALUE;
+    if (dim > kNaMaxDim) return PARAMENT_ERR_UNSUPPORTED;
     if (dtype != PARAMENT_C64 && dtype != PARAMENT_C128) return PARAMENT_ERR_INVALID_VALUE;
+    if (cdtype != PARAMENT_F32 && cdtype != PARAMENT_F64) return PARAMENT_ERR_INVALID_VALUE;
     if (integrator != PARAMENT_MIDPOINT && integrator != PARAMENT_MAGNUS4_GL2 &&
         integrator != PARAMENT_MAGNUS4_SIMPSON)
         return PARAMENT_ERR_INVALID_VALUE;
     if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32) return PARAMENT_ERR_UNSUPPORTED;
     const int fp64 = prec == PARAMENT_PREC_FP64;
     if ((cdtype == PARAMENT_F64) != (fp64 != 0)) return PARAMENT_ERR_INVALID_VALUE;  // no conversion buffer
-    if (n_steps < 0 || n_steps > (int64_t)0x7fffffff || !std::isfinite(dt)) return PARAMENT_ERR_INVALID_VALUE;
+    if (n_steps < 0 || n_steps > (int64_t)0x7fffffff) return PARAMENT_ERR_INVALID_VALUE;
+    if (!std::isfinite(dt)) return PARAMENT_ERR_NONFINITE;
     const int magnus = integrator != PARAMENT_MIDPOINT;
     const int nb = magnus ? 1 + 2 * n_ctrl + n_ctrl * (n_ctrl - 1) / 2 : 1 + n_ctrl;
     if (nb > kNaMaxBasis) return PARAMENT_ERR_UNSUPPORTED;
@@ -98,6 +102,10 @@ extern "C" int parament_propagate_noalloc(int dim, int n_ctrl, const void *H0, c
     if (!H0 || !U_out || (n_ctrl > 0 && !Hk) || (need_c && !c)) return PARAMENT_ERR_INVALID_VALUE;
     if (!on_device(H0) || !on_device(U_out) || (n_ctrl > 0 && !on_device(Hk)) || (need_c && !on_device(c)))
         return PARAMENT_ERR_INVALID_VALUE;
+    // the kernel stores U as float2 / double2 and reads c as float / double: misaligned pointers
+    // would fault in the kernel, so they are refused here
+    const size_t esz_u = dtype == PARAMENT_C128 ? 16 : 8, esz_c = fp64 ? 8 : 4;
+    if ((uintptr_t)U_out % esz_u != 0 || (need_c && (uintptr_t)c % esz_c != 0)) return PARAMENT_ERR_INVALID_VALUE;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -171,6 +179,12 @@ extern "C" int parament_propagate_noalloc(int dim, int n_ctrl, const void *H0, c
     p.extra_squarings = 0;
     p.unitary_step = fp64 ? 0 : 1;  // as parament_propagate with its default options
     NA_CUDA(pm::fused_launch(Dp, fp64, (int)integrator, p, (int)grid, warps, smem, stream));
+    if (device_status) {
+        // the root of the product tree moved the status bits of this call to the second word
+        NA_CUDA(cudaMemcpyAsync(device_status, base + kOffStat + sizeof(unsigned), sizeof(unsigned),
+                                cudaMemcpyDeviceToHost, stream));
+        NA_CUDA(cudaStreamSynchronize(stream));
+    }
 #undef NA_CUDA
     (void)DD;
     return PARAMENT_OK;
