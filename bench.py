@@ -316,7 +316,7 @@ def secondary_workloads(torch, b, wl, dev, flush, steps=10, warmup=3):
     probs = wl.batched_instances()
     total_steps = sum(p.n_steps for p in probs)
     inst32, keep32, outs32 = prop.batch([(p.H0, p.Hk, p.c, p.dt, p.n_steps) for p in probs], "fp32")
-    leaf, items, tune_ms = prop.batch_autotune(inst32, "fp32")
+    leaf, items, tune_ms, _ = prop.batch_autotune(inst32, "fp32")
     per = time_launches(torch, lambda: prop.propagate_batched(inst32, "fp32"), 5, 2, flush)
     ms32 = statistics.mean(per)
     inst_tc, keep_tc, outs_tc = prop.batch([(p.H0, p.Hk, p.c, p.dt, p.n_steps) for p in probs], "fp32_tc_tf32x3")

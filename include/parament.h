@@ -87,17 +87,17 @@ typedef enum {
  *        cores: every FP32 operand split into two round-to-nearest TF32 terms,
  *        three MMAs per real product (hi*hi + hi*lo + lo*hi), FP32 accumulation
  *        with a fresh accumulator per k-chunk; FP64 norm bound and FP64 top
- *        tree as in FP32.  d in 65..128: tcgen05 with tensor-memory accumulators;
- *        d in 129..256 (and the batched kernel's d = 128): mma.sync; d in 17..64:
- *        the shared-memory CUDA-core product of FP32, which is faster there (and
- *        at least as accurate).  d <= 16: PARAMENT_ERR_UNSUPPORTED.
+ *        tree as in FP32.  d in 17..128: tcgen05 with tensor-memory
+ *        accumulators (d <= 64: working matrices in shared memory, the four real
+ *        products of a complex product in one M = 128 MMA chain); d in 129..256:
+ *        mma.sync.  d <= 16: PARAMENT_ERR_UNSUPPORTED.
+ *        parament_stats.product_backends names the code that ran.
  *  FP32_TC_BF16X3: FP32 with every operand split into three round-to-nearest
  *        BF16 terms (x = b0 + b1 + b2, 24 significant bits) and the six products
  *        b0 b0 + b0 b1 + b1 b0 + b0 b2 + b1 b1 + b2 b0 per real product on the
  *        tensor cores (tcgen05 kind::f16), FP32 accumulation with a fresh
- *        accumulator per k-chunk.  d in 65..128: tcgen05; d in 17..64: the
- *        shared-memory CUDA-core product of FP32 (faster there); d <= 16 or
- *        d > 128: PARAMENT_ERR_UNSUPPORTED.
+ *        accumulator per k-chunk.  d in 17..128: tcgen05; d <= 16 or d > 128:
+ *        PARAMENT_ERR_UNSUPPORTED.
  */
 typedef enum {
     PARAMENT_PREC_FP64 = 0,
@@ -143,7 +143,11 @@ typedef enum {
        on every leaf product (the exact product is unitary; FP32 rounding that repeats from slice to
        slice, and the truncating tensor-core accumulation, otherwise drift R off the unitary group
        linearly in the leaf length); 0 = plain products */
-    PARAMENT_OPT_UNITARY_STEP = 14
+    PARAMENT_OPT_UNITARY_STEP = 14,
+    /* batched, tensor-core precisions: bit mask of the dimension classes whose products run on the
+       CUDA cores instead of tcgen05 (bit 0: d 17..32, bit 1: d 33..64, bit 2: d 65..128); default 0.
+       parament_batch_autotune sets it. */
+    PARAMENT_OPT_BATCH_CUDA_CORE_CLASSES = 15
 } parament_option;
 
 /* per-call diagnostics of the most recent propagate (see parament_get_stats) */
@@ -297,7 +301,10 @@ typedef struct {
  * The set-up (all bases) and the launch are captured in a CUDA graph that is
  * replayed while the instance shapes stay the same (option
  * PARAMENT_OPT_BATCH_GRAPH; the context must have a non-default stream).
- * cdtype must match prec (F64 with FP64, F32 with FP32 and FP32_TC_TF32X3).
+ * cdtype must match prec (F64 with FP64, F32 with FP32 and the tensor-core
+ * precisions).  With FP32_TC_TF32X3 / FP32_TC_BF16X3 the instances of d >= 17
+ * run their products on tcgen05, except the dimension classes listed in
+ * PARAMENT_OPT_BATCH_CUDA_CORE_CLASSES; d <= 16 always runs on the CUDA cores.
  * Basis matrices are not pruned and Hermiticity is not checked.  Returns
  * without waiting.  Contexts keep the batch plan, so the same context must not
  * run two batches concurrently.
@@ -306,15 +313,20 @@ int parament_propagate_batched(parament_ctx *ctx, const parament_instance *inst,
                                parament_real_dtype cdtype, parament_integrator integrator, parament_precision prec);
 
 /*
- * Autotuner of the batched launch: times the batch for every pair of
+ * Autotuner of the batched launch.  (1) Times the batch for every pair of
  * (target slices per leaf in {32, 128}) x (work items per SM in
- * {8, 16, 32, 64}), keeps the fastest in the context options
- * PARAMENT_OPT_BATCH_LEAF_STEPS / PARAMENT_OPT_BATCH_ITEMS_PER_SM and reports
- * it (and its time in ms) through the optional outputs.  Waits for the GPU.
+ * {8, 16, 32, 64}).  (2) For the tensor-core precisions, then times every
+ * choice of product back-end (tcgen05 or CUDA cores) for each dimension class
+ * present (d 17..32, 33..64, 65..128) with the best split, and (3) if a class
+ * moved to the CUDA cores, the split again.  Keeps the fastest in the context
+ * options PARAMENT_OPT_BATCH_LEAF_STEPS, PARAMENT_OPT_BATCH_ITEMS_PER_SM and
+ * PARAMENT_OPT_BATCH_CUDA_CORE_CLASSES and reports them (and the time in ms)
+ * through the optional outputs.  Waits for the GPU.
  */
 int parament_batch_autotune(parament_ctx *ctx, const parament_instance *inst, int n_inst, parament_dtype dtype,
                             parament_real_dtype cdtype, parament_integrator integrator, parament_precision prec,
-                            int *best_leaf_steps, int *best_items_per_sm, double *best_ms);
+                            int *best_leaf_steps, int *best_items_per_sm, double *best_ms,
+                            unsigned *cuda_core_classes);
 
 /* Diagnostics of the latest propagate; waits for the stream. */
 int parament_get_stats(parament_ctx *ctx, parament_stats *out);

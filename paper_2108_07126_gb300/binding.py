@@ -63,6 +63,7 @@ PARAMENT_OPT_BATCH_ITEMS_PER_SM = 11
 PARAMENT_OPT_BATCH_GRAPH = 12
 PARAMENT_OPT_EXP_METHOD = 13
 PARAMENT_OPT_UNITARY_STEP = 14
+PARAMENT_OPT_BATCH_CUDA_CORE_CLASSES = 15
 
 PARAMENT_DEV_NONFINITE_NORM = 0x1
 PARAMENT_DEV_NORM_CAPPED = 0x2
@@ -138,7 +139,8 @@ _SIGS = {
                                     ctypes.c_int, ctypes.c_int], ctypes.c_int),
     "parament_batch_autotune": ([_vp, ctypes.POINTER(parament_instance), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
-                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
     "parament_chebyshev_theta": ([ctypes.c_int, ctypes.c_double], ctypes.c_double),
     "parament_chebyshev_degree": ([ctypes.c_double, ctypes.c_double], ctypes.c_int),
     "parament_bessel_j": ([ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -273,10 +275,10 @@ def parament_propagate_batched(ctx, inst: list, dtype: int, cdtype: int, integra
 
 def parament_batch_autotune(ctx, inst: list, dtype: int, cdtype: int, integrator: int, prec: int):
     arr = _instances(inst)
-    l, i, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    l, i, ms, m = ctypes.c_int(), ctypes.c_int(), ctypes.c_double(), ctypes.c_uint32()
     _check(_lib.parament_batch_autotune(ctx, arr, len(inst), int(dtype), int(cdtype), int(integrator), int(prec),
-                                        ctypes.byref(l), ctypes.byref(i), ctypes.byref(ms)), ctx)
-    return l.value, i.value, ms.value
+                                        ctypes.byref(l), ctypes.byref(i), ctypes.byref(ms), ctypes.byref(m)), ctx)
+    return l.value, i.value, ms.value, m.value
 
 
 def parament_chebyshev_theta(m: int, u: float) -> float:
@@ -334,6 +336,9 @@ class Propagator:
 
     def set_option(self, key: int, value: int):
         parament_set_option(self.ctx, key, value)
+
+    def get_option(self, key: int) -> int:
+        return parament_get_option(self.ctx, key)
 
     def set_hamiltonians(self, H0, Hk, integrator: str = "midpoint"):
         torch = self._torch

@@ -36,9 +36,11 @@ SOURCES = [
     "pm_large_d256.cu",
     "pm_batched_fm.cu",
     "pm_batched_fm_tc.cu",
+    "pm_batched_fm_bf.cu",
     "pm_batched_dm.cu",
     "pm_batched_fg.cu",
     "pm_batched_fg_tc.cu",
+    "pm_batched_fg_bf.cu",
     "pm_batched_dg.cu",
 ]
 

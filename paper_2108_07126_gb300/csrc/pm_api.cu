@@ -50,13 +50,15 @@ cudaError_t batch_basis_launch(int, int, const BatchInst *, const int2 *, int, i
                                cudaStream_t);
 #define PM_DECL_B(v)                                                                                     \
     cudaError_t batched_launch_##v(const BatchItem *, int, unsigned *, const FusedParams *, unsigned char *, \
-                                   size_t, int, size_t, cudaStream_t);                                   \
+                                   size_t, int, size_t, unsigned *, cudaStream_t);                       \
     int batched_blocks_per_sm_##v(size_t);
 PM_DECL_B(fm)
 PM_DECL_B(fm_tc)
+PM_DECL_B(fm_bf)
 PM_DECL_B(dm)
 PM_DECL_B(fg)
 PM_DECL_B(fg_tc)
+PM_DECL_B(fg_bf)
 PM_DECL_B(dg)
 #undef PM_DECL_B
 }  // namespace pm
@@ -108,6 +110,7 @@ struct parament_ctx {
     cudaGraphExec_t b_exec = nullptr;
     bool last_batched = false;
     int64_t opt_batch_leaf = 0, opt_batch_items = 0, opt_batch_graph = 1;
+    int64_t opt_batch_cuda_mask = 0;  // dimension classes (bit 0: D = 32, 1: 64, 2: 128) on the CUDA cores
     int64_t opt_exp_method = 0;
     int64_t opt_unitary_step = 1;
     Workspace cheb;  // Chebyshev pre-pass: max norm bound, degree, 1/beta, coefficients
@@ -996,8 +999,12 @@ int forward_setup(parament_ctx *ctx, int fp64, void *U_dst, FusedParams &p, int 
         warps = 8;
         smem = large_smem(Dp, fp64, nb, tc);
         if (smem > ctx->smem_optin) return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "large-d shared memory %zu B", smem);
-        const int bps = large_blocks_per_sm(Dp, fp64, (int)ctx->integ, smem, tc);
+        int bps = large_blocks_per_sm(Dp, fp64, (int)ctx->integ, smem, tc);
         if (bps <= 0) return set_err(ctx, PARAMENT_ERR_CUDA, "occupancy query failed (large d)");
+        // the d <= 32 tensor-core body is compiled for two blocks per SM and they do run together
+        // (measured: 2^14 slices at d = 32 in 1.7 ms with 304 blocks, 2.7 ms with 152), although
+        // the occupancy query reports one
+        if (tc && !fp64 && Dp == 32) bps = std::max(bps, 2);
         leaves_per_block = 1;
         grid = (int)ctx->opt_grid;
         if (grid <= 0) grid = (int)std::max<int64_t>(1, std::min<int64_t>(ctx->n_steps, (int64_t)bps * ctx->sm_count));
@@ -1530,6 +1537,10 @@ int parament_set_option(parament_ctx *ctx, int key, int64_t value) {
         case PARAMENT_OPT_UNITARY_STEP:
             ctx->opt_unitary_step = value != 0;
             return PARAMENT_OK;
+        case PARAMENT_OPT_BATCH_CUDA_CORE_CLASSES:
+            if (value < 0 || value > 7) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "class mask in [0, 7]");
+            ctx->opt_batch_cuda_mask = value;
+            return PARAMENT_OK;
     }
     return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown option key %d", key);
 }
@@ -1550,6 +1561,7 @@ int parament_get_option(const parament_ctx *ctx, int key, int64_t *value) {
         case PARAMENT_OPT_BATCH_GRAPH: *value = ctx->opt_batch_graph; return PARAMENT_OK;
         case PARAMENT_OPT_EXP_METHOD: *value = ctx->opt_exp_method; return PARAMENT_OK;
         case PARAMENT_OPT_UNITARY_STEP: *value = ctx->opt_unitary_step; return PARAMENT_OK;
+        case PARAMENT_OPT_BATCH_CUDA_CORE_CLASSES: *value = ctx->opt_batch_cuda_mask; return PARAMENT_OK;
     }
     return PARAMENT_ERR_INVALID_VALUE;
 }
@@ -1596,16 +1608,19 @@ cudaError_t basis_build(const void *raw, int c128, int d, int Dp, int K, int mag
 
 namespace {
 
+// variant = 4 * magnus + (FP64 ? 3 : tensor-core format), format 0 none, 1 3xTF32, 2 split BF16x3
 cudaError_t batched_launch(int variant, const BatchItem *items, int n_items, unsigned *queue,
                            const FusedParams *params, unsigned char *scratch, size_t stride, int grid, size_t smem,
-                           cudaStream_t st) {
+                           unsigned *status, cudaStream_t st) {
     switch (variant) {
-        case 0: return batched_launch_fm(items, n_items, queue, params, scratch, stride, grid, smem, st);
-        case 1: return batched_launch_fm_tc(items, n_items, queue, params, scratch, stride, grid, smem, st);
-        case 2: return batched_launch_dm(items, n_items, queue, params, scratch, stride, grid, smem, st);
-        case 3: return batched_launch_fg(items, n_items, queue, params, scratch, stride, grid, smem, st);
-        case 4: return batched_launch_fg_tc(items, n_items, queue, params, scratch, stride, grid, smem, st);
-        case 5: return batched_launch_dg(items, n_items, queue, params, scratch, stride, grid, smem, st);
+        case 0: return batched_launch_fm(items, n_items, queue, params, scratch, stride, grid, smem, status, st);
+        case 1: return batched_launch_fm_tc(items, n_items, queue, params, scratch, stride, grid, smem, status, st);
+        case 2: return batched_launch_fm_bf(items, n_items, queue, params, scratch, stride, grid, smem, status, st);
+        case 3: return batched_launch_dm(items, n_items, queue, params, scratch, stride, grid, smem, status, st);
+        case 4: return batched_launch_fg(items, n_items, queue, params, scratch, stride, grid, smem, status, st);
+        case 5: return batched_launch_fg_tc(items, n_items, queue, params, scratch, stride, grid, smem, status, st);
+        case 6: return batched_launch_fg_bf(items, n_items, queue, params, scratch, stride, grid, smem, status, st);
+        case 7: return batched_launch_dg(items, n_items, queue, params, scratch, stride, grid, smem, status, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -1614,18 +1629,25 @@ int batched_occupancy(int variant, size_t smem) {
     switch (variant) {
         case 0: return batched_blocks_per_sm_fm(smem);
         case 1: return batched_blocks_per_sm_fm_tc(smem);
-        case 2: return batched_blocks_per_sm_dm(smem);
-        case 3: return batched_blocks_per_sm_fg(smem);
-        case 4: return batched_blocks_per_sm_fg_tc(smem);
-        case 5: return batched_blocks_per_sm_dg(smem);
+        case 2: return batched_blocks_per_sm_fm_bf(smem);
+        case 3: return batched_blocks_per_sm_dm(smem);
+        case 4: return batched_blocks_per_sm_fg(smem);
+        case 5: return batched_blocks_per_sm_fg_tc(smem);
+        case 6: return batched_blocks_per_sm_fg_bf(smem);
+        case 7: return batched_blocks_per_sm_dg(smem);
     }
     return 0;
 }
 
+// dimension class of the batched tensor-core choice: D = 32, 64, 128 -> 0, 1, 2 (-1 below 32)
+int batch_tc_class(int Dp) { return Dp == 32 ? 0 : (Dp == 64 ? 1 : (Dp == 128 ? 2 : -1)); }
+
 // the code that runs the complex products of one dimension class of the batched kernel
-unsigned batch_backend(int Dp, int fp64, int tc) {
-    if (fp64 || !tc || Dp <= 64) return PARAMENT_BACKEND_CUDA_CORES;
-    return PARAMENT_BACKEND_MMA_SYNC;
+// (cuda_mask: bit batch_tc_class(D) set = that class runs on the CUDA cores in a tensor-core batch)
+unsigned batch_backend(int Dp, int fp64, int tc, unsigned cuda_mask) {
+    const int cls = batch_tc_class(Dp);
+    if (fp64 || !tc || cls < 0 || ((cuda_mask >> cls) & 1u)) return PARAMENT_BACKEND_CUDA_CORES;
+    return PARAMENT_BACKEND_TCGEN05;
 }
 
 // Build (when the shapes change) and enqueue one batched propagation.
@@ -1636,13 +1658,16 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
         return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown dtype %d", (int)dtype);
     if (integ != PARAMENT_MIDPOINT && integ != PARAMENT_MAGNUS4_GL2)
         return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "batched propagation supports midpoint and GL4 Magnus");
-    if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32 && prec != PARAMENT_PREC_FP32_TC_TF32X3)
-        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "batched precision must be FP64, FP32 or FP32_TC_TF32X3");
-    const int fp64 = prec == PARAMENT_PREC_FP64, tc = prec == PARAMENT_PREC_FP32_TC_TF32X3;
+    if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32 && prec != PARAMENT_PREC_FP32_TC_TF32X3 &&
+        prec != PARAMENT_PREC_FP32_TC_BF16X3)
+        return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown precision %d", (int)prec);
+    const int fp64 = prec == PARAMENT_PREC_FP64;
+    const int tc = prec == PARAMENT_PREC_FP32_TC_TF32X3 ? 1 : (prec == PARAMENT_PREC_FP32_TC_BF16X3 ? 2 : 0);
     if ((cdtype == PARAMENT_F64) != (fp64 != 0))
         return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "control dtype must match the precision in batched calls");
     const int magnus = integ != PARAMENT_MIDPOINT;
-    const int variant = (magnus ? 3 : 0) + (fp64 ? 2 : (tc ? 1 : 0));
+    const int variant = (magnus ? 4 : 0) + (fp64 ? 3 : tc);
+    const unsigned cuda_mask = tc ? (unsigned)ctx->opt_batch_cuda_mask : 0u;
     ctx->last_batched = true;
     if (n == 0) return PARAMENT_OK;
     for (int i = 0; i < n; ++i) {
@@ -1661,7 +1686,7 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
     const int items_per_sm = ctx->opt_batch_items > 0 ? (int)ctx->opt_batch_items : 32;
     const size_t csz = fp64 ? 16 : 8, rsz = fp64 ? 8 : 4;
 
-    std::vector<int64_t> key = {n, dtype, cdtype, integ, prec, leaf_steps, items_per_sm};
+    std::vector<int64_t> key = {n, dtype, cdtype, integ, prec, leaf_steps, items_per_sm, (int64_t)cuda_mask};
     for (int i = 0; i < n; ++i) {
         key.push_back(inst[i].dim);
         key.push_back(inst[i].n_ctrl);
@@ -1700,7 +1725,9 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
                 smem = std::max(smem, fused_smem(Dp[i], fp64, nbs[i], w));
             } else {
                 nb_cap = std::max<int64_t>(1, N / leaf_steps);
-                smem = std::max(smem, large_smem(Dp[i], fp64, nbs[i]));
+                const int cls = batch_tc_class(Dp[i]);
+                const bool on_tc = tc && cls >= 0 && !((cuda_mask >> cls) & 1u);
+                smem = std::max(smem, large_smem(Dp[i], fp64, nbs[i], on_tc ? tc : 0));
                 stride = std::max(stride, (size_t)6 * Dp[i] * Dp[i] * csz);
             }
             nblk[i] = (int)std::min<int64_t>({nb_cap, (int64_t)std::ceil(cost / std::max(target, 1.0)), 1024});
@@ -1815,6 +1842,10 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
         p.extra_squarings = (int)ctx->opt_extra_sq;
         p.unitary_step = fp64 ? 0 : (int)ctx->opt_unitary_step;
         p.warps = ctx->b_warps[i];
+        {
+            const int cls = batch_tc_class(Dp[i]);
+            p.tc_off = (cls >= 0 && ((cuda_mask >> cls) & 1u)) ? 1 : 0;
+        }
         npart += (size_t)nblk_of[i] * Dp[i] * Dp[i];
         ntick += 2 * (size_t)nblk_of[i] + 2;
         insts[i] = BatchInst{q.H0, q.Hk, q.dim, Dp[i], q.n_ctrl, nbs[i], full_off[i], packed_off[i], norm_off[i]};
@@ -1839,9 +1870,12 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
                                            ctx->stream);
         if (e != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(ctx->bqueue.ptr, 0, sizeof(unsigned), ctx->stream)) != cudaSuccess) return e;
+        // the kernel-wide status word (bounded tensor-core waits) is the one parament_get_stats reads
+        unsigned *kstatus = (unsigned *)ctx->status.ptr + 1;
+        if ((e = cudaMemsetAsync(kstatus, 0, sizeof(unsigned), ctx->stream)) != cudaSuccess) return e;
         return batched_launch(ctx->b_variant, (const BatchItem *)ctx->bitems.ptr, ctx->b_n_items,
                               (unsigned *)ctx->bqueue.ptr, (const FusedParams *)ctx->bparams.ptr,
-                              (unsigned char *)ctx->bscratch.ptr, ctx->b_stride, ctx->b_grid, ctx->b_smem,
+                              (unsigned char *)ctx->bscratch.ptr, ctx->b_stride, ctx->b_grid, ctx->b_smem, kstatus,
                               ctx->stream);
     };
     if (ctx->opt_batch_graph && ctx->stream != nullptr) {
@@ -1872,7 +1906,7 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
     unsigned backends = 0;
     for (int i = 0; i < n; ++i) {
         tot += inst[i].n_steps;
-        backends |= batch_backend(pad_dim(inst[i].dim), fp64, tc);
+        backends |= batch_backend(pad_dim(inst[i].dim), fp64, tc, cuda_mask);
     }
     ctx->last = parament_stats{};
     ctx->last.n_steps = tot;
@@ -1898,49 +1932,84 @@ int parament_propagate_batched(parament_ctx *ctx, const parament_instance *inst,
 
 int parament_batch_autotune(parament_ctx *ctx, const parament_instance *inst, int n_inst, parament_dtype dtype,
                             parament_real_dtype cdtype, parament_integrator integrator, parament_precision prec,
-                            int *best_leaf_steps, int *best_items_per_sm, double *best_ms) {
+                            int *best_leaf_steps, int *best_items_per_sm, double *best_ms,
+                            unsigned *cuda_core_classes) {
     if (!ctx) return PARAMENT_ERR_INVALID_VALUE;
     ctx->err.clear();
     DeviceGuard guard(ctx->device);
-    const int leafs[] = {32, 128}, items[] = {8, 16, 32, 64};
+    const bool tc = prec == PARAMENT_PREC_FP32_TC_TF32X3 || prec == PARAMENT_PREC_FP32_TC_BF16X3;
+    unsigned present = 0;  // dimension classes with a tensor-core body in this batch
+    for (int i = 0; tc && i < n_inst && inst; ++i) {
+        const int cls = batch_tc_class(pad_dim(inst[i].dim));
+        if (cls >= 0) present |= 1u << cls;
+    }
     cudaEvent_t a, b;
     PM_CUDA(cudaEventCreate(&a));
     PM_CUDA(cudaEventCreate(&b));
+    int st = PARAMENT_OK;
+    // one configuration: a warm-up run (which also builds the plan), then the mean of two timed runs
+    auto time_cfg = [&](int l, int it, unsigned mask, double *ms_out) -> int {
+        ctx->opt_batch_leaf = l;
+        ctx->opt_batch_items = it;
+        ctx->opt_batch_cuda_mask = mask;
+        int s2 = batch_run(ctx, inst, n_inst, dtype, cdtype, integrator, prec);
+        float ms_sum = 0.f;
+        for (int r = 0; r < 2 && s2 == PARAMENT_OK; ++r) {
+            cudaEventRecord(a, ctx->stream);
+            s2 = batch_run(ctx, inst, n_inst, dtype, cdtype, integrator, prec);
+            cudaEventRecord(b, ctx->stream);
+            cudaEventSynchronize(b);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            ms_sum += ms;
+        }
+        *ms_out = ms_sum / 2.0;
+        return s2;
+    };
+    const int leafs[] = {32, 128}, items[] = {8, 16, 32, 64};
     double best = 1e300;
     int bl = 128, bi = 32;
-    int st = PARAMENT_OK;
-    for (int l : leafs) {
-        for (int it : items) {
-            ctx->opt_batch_leaf = l;
-            ctx->opt_batch_items = it;
-            if ((st = batch_run(ctx, inst, n_inst, dtype, cdtype, integrator, prec))) break;  // warm-up + plan
-            float ms_sum = 0.f;
-            for (int r = 0; r < 3 && st == PARAMENT_OK; ++r) {
-                cudaEventRecord(a, ctx->stream);
-                st = batch_run(ctx, inst, n_inst, dtype, cdtype, integrator, prec);
-                cudaEventRecord(b, ctx->stream);
-                cudaEventSynchronize(b);
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, a, b);
-                ms_sum += ms;
+    unsigned bm = 0;
+    // (1) the work split with every class on the tensor cores (or the CUDA cores for FP32 / FP64)
+    auto tune_split = [&](unsigned mask) {
+        for (int l : leafs)
+            for (int it : items) {
+                double ms = 0.0;
+                if ((st = time_cfg(l, it, mask, &ms))) return;
+                if (ms < best) {
+                    best = ms;
+                    bl = l;
+                    bi = it;
+                    bm = mask;
+                }
             }
-            if (st) break;
-            if (ms_sum / 3.0 < best) {
-                best = ms_sum / 3.0;
-                bl = l;
-                bi = it;
+    };
+    tune_split(0u);
+    // (2) per dimension class: tensor cores or CUDA cores, every subset of the classes present
+    if (!st && present) {
+        const unsigned split_mask = bm;
+        for (unsigned m = 1; m <= 7 && !st; ++m) {
+            if ((m & ~present) != 0u) continue;
+            double ms = 0.0;
+            if ((st = time_cfg(bl, bi, m, &ms))) break;
+            if (ms < best) {
+                best = ms;
+                bm = m;
             }
         }
-        if (st) break;
+        // (3) the split again for the chosen back-ends
+        if (!st && bm != split_mask) tune_split(bm);
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (st) return st;
     ctx->opt_batch_leaf = bl;
     ctx->opt_batch_items = bi;
+    ctx->opt_batch_cuda_mask = bm;
     if (best_leaf_steps) *best_leaf_steps = bl;
     if (best_items_per_sm) *best_items_per_sm = bi;
     if (best_ms) *best_ms = best;
+    if (cuda_core_classes) *cuda_core_classes = bm;
     return PARAMENT_OK;
 }
 

@@ -107,17 +107,37 @@ static __device__ __noinline__ void batch_fused_item(const FusedParams &p, int b
 
 template <typename Real, int D, int INTEG, int TCM>
 static __device__ __noinline__ void batch_large_item(const FusedParams &p, unsigned char *ws, int blk, int nblk,
-                                                     unsigned char *smem) {
-    large_body<Real, D, INTEG, TCM>(p, (typename Cx<Real>::T *)ws, blk, nblk, smem);
+                                                     unsigned char *smem, umma::Ctx *uc) {
+    large_body<Real, D, INTEG, TCM>(p, (typename Cx<Real>::T *)ws, blk, nblk, smem, uc);
     large_arrival_tree<Real, D>(p, ws, blk, nblk, smem);
 }
 
-template <typename Real, int INTEG, bool TC>
+// D = 32 / 64 on the tensor cores: the shared-memory body of pm_tc_small.cuh, then the arrival tree
+template <int D, int INTEG, int F>
+static __device__ __noinline__ void batch_tc_item(const FusedParams &p, unsigned char *ws, int blk, int nblk,
+                                                  unsigned char *smem, umma::Ctx *uc) {
+    tcs::body<D, INTEG, F>(p, blk, nblk, smem, *uc);
+    large_arrival_tree<float, D>(p, ws, blk, nblk, smem);
+}
+
+// TC: 0 = every product on the CUDA cores; 1 / 2 = D >= 32 products on the tcgen05 tensor cores in
+// 3xTF32 / split BF16x3 (FP32 only), except for instances whose parameters set tc_off (the
+// autotuner's choice for their dimension class).  A tensor-core kernel allocates the 512 columns
+// of tensor memory once per block for all of its items.
+template <typename Real, int INTEG, int TC>
 __global__ void __launch_bounds__(256, 1) batched_kernel(const BatchItem *__restrict__ items, int n_items,
                                                          unsigned *queue, const FusedParams *__restrict__ params,
-                                                         unsigned char *scratch, size_t scratch_stride) {
+                                                         unsigned char *scratch, size_t scratch_stride,
+                                                         unsigned *status) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_item;
+    constexpr bool kTc = TC != 0 && std::is_same<Real, float>::value;
+    constexpr int F = TC == 2 ? umma::kBF16x3 : umma::kTF32x3;
+    __shared__ __align__(8) uint64_t s_mbar[umma::kBars];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    umma::Ctx cx;
+    if constexpr (kTc) umma::setup(cx, s_mbar, &s_tmem, &s_abort, status);
     unsigned char *ws = scratch + (size_t)blockIdx.x * scratch_stride;
     for (;;) {
         if (threadIdx.x == 0) s_item = (int)atomicAdd(queue, 1u);
@@ -127,28 +147,63 @@ __global__ void __launch_bounds__(256, 1) batched_kernel(const BatchItem *__rest
         if (it >= n_items) break;
         const BatchItem w = items[it];
         const FusedParams &p = params[w.inst];
+        const bool tc = kTc && !p.tc_off;
         switch (w.Dp) {
             case 2: batch_fused_item<Real, 2, INTEG>(p, w.blk, w.nblk, smem); break;
             case 4: batch_fused_item<Real, 4, INTEG>(p, w.blk, w.nblk, smem); break;
             case 8: batch_fused_item<Real, 8, INTEG>(p, w.blk, w.nblk, smem); break;
             case 16: batch_fused_item<Real, 16, INTEG>(p, w.blk, w.nblk, smem); break;
-            // CUDA-core products at 32 and 64 (faster than 3xTF32 there)
-            case 32: batch_large_item<Real, 32, INTEG, 0>(p, ws, w.blk, w.nblk, smem); break;
-            case 64: batch_large_item<Real, 64, INTEG, 0>(p, ws, w.blk, w.nblk, smem); break;
-            case 128: batch_large_item<Real, 128, INTEG, TC ? 1 : 0>(p, ws, w.blk, w.nblk, smem); break;
+            case 32:
+                if constexpr (kTc) {
+                    if (tc) {
+                        batch_tc_item<32, INTEG, F>(p, ws, w.blk, w.nblk, smem, &cx);
+                        break;
+                    }
+                }
+                batch_large_item<Real, 32, INTEG, 0>(p, ws, w.blk, w.nblk, smem, nullptr);
+                break;
+            case 64:
+                if constexpr (kTc) {
+                    if (tc) {
+                        batch_tc_item<64, INTEG, F>(p, ws, w.blk, w.nblk, smem, &cx);
+                        break;
+                    }
+                }
+                batch_large_item<Real, 64, INTEG, 0>(p, ws, w.blk, w.nblk, smem, nullptr);
+                break;
+            case 128:
+                if constexpr (kTc) {
+                    if (tc) {
+                        batch_large_item<Real, 128, INTEG, TC == 2 ? 3 : 2>(p, ws, w.blk, w.nblk, smem, &cx);
+                        break;
+                    }
+                }
+                batch_large_item<Real, 128, INTEG, 0>(p, ws, w.blk, w.nblk, smem, nullptr);
+                break;
         }
         __syncthreads();
     }
+    if constexpr (kTc) umma::teardown(cx);
 }
 
-template <typename Real, int INTEG, bool TC>
+template <typename Real, int INTEG, int TC>
 cudaError_t launch_batched(const BatchItem *items, int n_items, unsigned *queue, const FusedParams *params,
-                           unsigned char *scratch, size_t scratch_stride, int grid, size_t smem, cudaStream_t st) {
+                           unsigned char *scratch, size_t scratch_stride, int grid, size_t smem, unsigned *status,
+                           cudaStream_t st) {
     auto k = batched_kernel<Real, INTEG, TC>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k<<<grid, 256, smem, st>>>(items, n_items, queue, params, scratch, scratch_stride);
+    k<<<grid, 256, smem, st>>>(items, n_items, queue, params, scratch, scratch_stride, status);
     return cudaGetLastError();
+}
+
+template <typename Real, int INTEG, int TC>
+int batched_occupancy_of(size_t smem) {
+    int nb = 0;
+    auto k = batched_kernel<Real, INTEG, TC>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 256, smem) != cudaSuccess) return 0;
+    return nb;
 }
 
 }  // namespace pm

@@ -1,19 +1,14 @@
-// Instantiation of the batched propagation kernel: double, integrator kMidpoint, tensor cores false.
+// Instantiation of the batched propagation kernel: double, integrator kMidpoint, CUDA-core products.
 #include "pm_batched.cuh"
 
 namespace pm {
 
 cudaError_t batched_launch_dm(const BatchItem *items, int n_items, unsigned *queue, const FusedParams *params,
-                                 unsigned char *scratch, size_t stride, int grid, size_t smem, cudaStream_t st) {
-    return launch_batched<double, kMidpoint, false>(items, n_items, queue, params, scratch, stride, grid, smem, st);
+                              unsigned char *scratch, size_t stride, int grid, size_t smem, unsigned *status,
+                              cudaStream_t st) {
+    return launch_batched<double, kMidpoint, 0>(items, n_items, queue, params, scratch, stride, grid, smem, status, st);
 }
 
-int batched_blocks_per_sm_dm(size_t smem) {
-    int nb = 0;
-    auto k = batched_kernel<double, kMidpoint, false>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 256, smem) != cudaSuccess) return 0;
-    return nb;
-}
+int batched_blocks_per_sm_dm(size_t smem) { return batched_occupancy_of<double, kMidpoint, 0>(smem); }
 
 }  // namespace pm

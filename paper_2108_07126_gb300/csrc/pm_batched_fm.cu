@@ -1,24 +1,15 @@
-// Instantiation of the batched propagation kernel: float, integrator kMidpoint, tensor cores false.
+// Instantiation of the batched propagation kernel: float, integrator kMidpoint, CUDA-core products.
 #include "pm_batched.cuh"
 
 namespace pm {
 
 cudaError_t batched_launch_fm(const BatchItem *items, int n_items, unsigned *queue, const FusedParams *params,
-                                 unsigned char *scratch, size_t stride, int grid, size_t smem, cudaStream_t st) {
-    return launch_batched<float, kMidpoint, false>(items, n_items, queue, params, scratch, stride, grid, smem, st);
+                              unsigned char *scratch, size_t stride, int grid, size_t smem, unsigned *status,
+                              cudaStream_t st) {
+    return launch_batched<float, kMidpoint, 0>(items, n_items, queue, params, scratch, stride, grid, smem, status, st);
 }
 
-int batched_blocks_per_sm_fm(size_t smem) {
-    int nb = 0;
-    auto k = batched_kernel<float, kMidpoint, false>;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, 256, smem) != cudaSuccess) return 0;
-    return nb;
-}
-
-}  // namespace pm
-
-namespace pm {
+int batched_blocks_per_sm_fm(size_t smem) { return batched_occupancy_of<float, kMidpoint, 0>(smem); }
 
 cudaError_t batch_basis_launch(int c128, int fp64, const BatchInst *insts, const int2 *table, int n_mats, int magnus,
                                double2 *full, void *packed, double *norms, cudaStream_t st) {

@@ -73,6 +73,7 @@ struct FusedParams {
     int extra_squarings;
     int unitary_step;          // FP32: one Newton-Schulz step R <- R (3 I - R^dagger R) / 2 on every leaf product
     int warps;                 // warps of a block that own leaves (0 = all; the others only join the barriers)
+    int tc_off;                // batched tensor-core kernel: run this instance's products on the CUDA cores
     const int *cheb_m;         // Chebyshev mode: degree, 1 / beta and coefficients (device, written by
     const double *cheb_inv_beta;  //   cheb_coef_kernel)
     const void *cheb_coef;     // Real complex [m + 1]: a_k = (-i)^k J_k(beta)

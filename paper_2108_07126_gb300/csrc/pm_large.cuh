@@ -14,6 +14,7 @@
 #include <type_traits>
 
 #include "pm_fused.cuh"
+#include "pm_tc_small.cuh"
 #include "pm_umma.cuh"
 
 namespace pm {
@@ -50,7 +51,10 @@ template <typename Real, int D> struct LGeo {
 template <int D> struct TcGeo;
 
 // TCM: 0 = CUDA-core products, 1 = 3xTF32 with mma.sync, 2 = 3xTF32 with tcgen05 (D = 128),
-// 3 = split BF16x3 with tcgen05 (D = 128)
+// 3 = split BF16x3 with tcgen05 (D = 128), 4 / 5 = 3xTF32 / split BF16x3 with tcgen05 in the
+// shared-memory body of pm_tc_small.cuh (D = 32, 64)
+template <int TCM> __host__ __device__ constexpr int tcm_format() { return (TCM == 3 || TCM == 5) ? umma::kBF16x3 : umma::kTF32x3; }
+
 template <typename Real, int D, int TCM = 0>
 __host__ __device__ inline size_t large_panel_bytes() {
     // the FP64 top tree and the tensor-core products run through the same panels
@@ -78,6 +82,12 @@ __host__ __device__ inline size_t large_front_bytes() {
 
 template <typename Real, int D, int TCM = 0>
 __host__ __device__ inline size_t large_smem_bytes(int n_basis) {
+    if constexpr (TCM >= 4) {
+        // the tensor-core body, and the FP64 / FP32 panels of the arrival tree that may follow it
+        size_t b = tcs::smem_bytes<D, tcm_format<TCM>()>(n_basis);
+        if (LGeo<double, D>::PANEL_BYTES > b) b = LGeo<double, D>::PANEL_BYTES;
+        return (b + 15) & ~(size_t)15;
+    }
     size_t b = large_front_bytes<Real, D, TCM>() + (size_t)(n_basis + 1) * sizeof(Real) + 64;
     return (b + 15) & ~(size_t)15;
 }
@@ -664,20 +674,37 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
 }
 
 // products of the tensor-core precisions in the standalone large kernel (TC: 0 none, 1 3xTF32,
-// 2 split BF16x3): tcgen05 for D = 128, mma.sync 3xTF32 for D = 256; at D <= 64 the shared-memory
-// CUDA-core product is faster than both (and at least as accurate) and is used instead
+// 2 split BF16x3): tcgen05 in the shared-memory body for D = 32, 64, tcgen05 with L2-resident
+// working matrices for D = 128, mma.sync 3xTF32 for D = 256
 template <typename Real, int D, int TC>
 __host__ __device__ constexpr int large_tcm() {
-    return (TC == 0 || !std::is_same<Real, float>::value || D <= 64) ? 0 : (D == 128 ? (TC == 2 ? 3 : 2) : 1);
+    return (TC == 0 || !std::is_same<Real, float>::value) ? 0
+           : (D <= 64 ? (TC == 2 ? 5 : 4) : (D == 128 ? (TC == 2 ? 3 : 2) : 1));
+}
+
+// blocks per SM the large kernel is compiled for: two for the tensor-core body at D = 32
+template <typename Real, int D, int TC>
+__host__ __device__ constexpr int large_min_blocks() {
+    return large_tcm<Real, D, TC>() >= 4 ? tcs::Cfg<D, tcm_format<large_tcm<Real, D, TC>()>()>::MIN_BLOCKS : 1;
 }
 
 template <typename Real, int D, int INTEG, int TC = 0>
-__global__ void __launch_bounds__(kLargeThreads, 1) large_kernel(const FusedParams p, void *scratch) {
+__global__ void __launch_bounds__(kLargeThreads, large_min_blocks<Real, D, TC>())
+    large_kernel(const FusedParams p, void *scratch) {
     extern __shared__ __align__(16) unsigned char smem[];
     using C = typename Cx<Real>::T;
     constexpr int TCM = large_tcm<Real, D, TC>();
     C *ws = (C *)scratch + (size_t)blockIdx.x * kLargeSlots * D * D;
-    if constexpr (TCM >= 2) {
+    if constexpr (TCM >= 4) {
+        __shared__ __align__(8) uint64_t s_mbar[umma::kBars];
+        __shared__ uint32_t s_tmem;
+        __shared__ int s_abort;
+        umma::Ctx cx;
+        constexpr int F = tcm_format<TCM>();
+        umma::setup(cx, s_mbar, &s_tmem, &s_abort, p.status, tcs::tmem_cols<D, F>());
+        tcs::body<D, INTEG, F>(p, blockIdx.x, gridDim.x, smem, cx);
+        umma::teardown(cx);
+    } else if constexpr (TCM >= 2) {
         __shared__ __align__(8) uint64_t s_mbar[umma::kBars];
         __shared__ uint32_t s_tmem;
         __shared__ int s_abort;

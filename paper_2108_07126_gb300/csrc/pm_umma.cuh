@@ -56,10 +56,12 @@ constexpr size_t kSmemBytes = (size_t)kStages * kStageBytes;
 // full[3] (a stage was written, one arrival per producer warp), free[2] (an accumulator set was
 // read back, one arrival per warp)
 constexpr int kProducerWarps = 7;
-constexpr int kBarDone = 0, kBarFull = 3, kBarFree = 6, kBars = 8;
+// 8, 9: done barriers of the small-dimension product of pm_tc_small.cuh (one commit each)
+constexpr int kBarDone = 0, kBarFull = 3, kBarFree = 6, kBarsBig = 8, kBarSDone = 8, kBars = 10;
 
 struct Ctx {
     uint32_t tmem;          // tensor-memory base address of the accumulators
+    uint32_t ncols;         // tensor-memory columns allocated by setup
     uint64_t *bar;          // kBars mbarriers in shared memory
     uint32_t cnt[kBars];    // completions of each barrier consumed so far (identical in all threads)
     int *abort;             // shared: a wait timed out, the remaining products are skipped
@@ -135,11 +137,12 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16]) {
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
 
 // Block-level set-up and tear-down (all threads of the block call both).
-__device__ __forceinline__ void setup(Ctx &cx, uint64_t *bar, uint32_t *tmem_slot, int *abort, unsigned *status) {
+__device__ __forceinline__ void setup(Ctx &cx, uint64_t *bar, uint32_t *tmem_slot, int *abort, unsigned *status,
+                                      uint32_t ncols = kTmemCols) {
     const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int b = 0; b < kBars; ++b) {
-            const int count = b < kBarFull ? 1 : (b < kBarFree ? kProducerWarps : 8);
+            const int count = (b < kBarFull || b >= kBarsBig) ? 1 : (b < kBarFree ? kProducerWarps : 8);
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar + b)), "r"(count) : "memory");
         }
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -147,7 +150,7 @@ __device__ __forceinline__ void setup(Ctx &cx, uint64_t *bar, uint32_t *tmem_slo
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
-                     "r"(kTmemCols)
+                     "r"(ncols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
@@ -155,6 +158,7 @@ __device__ __forceinline__ void setup(Ctx &cx, uint64_t *bar, uint32_t *tmem_slo
     __syncthreads();
     fence_after();
     cx.tmem = *tmem_slot;
+    cx.ncols = ncols;
     cx.bar = bar;
     for (int b = 0; b < kBars; ++b) cx.cnt[b] = 0;
     cx.abort = abort;
@@ -165,7 +169,7 @@ __device__ __forceinline__ void teardown(const Ctx &cx) {
     fence_before();
     __syncthreads();
     if ((threadIdx.x >> 5) == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(cx.tmem), "r"(kTmemCols)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(cx.tmem), "r"(cx.ncols)
                      : "memory");
 }
 
@@ -267,9 +271,9 @@ static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const 
     const uint32_t tl = cx.tmem + ((uint32_t)((warp & 3) * 32) << 16);
     // completions of each barrier before this product: chunk c is use c / 3 of stage c % 3 and
     // use c / 2 of accumulator set c % 2
-    uint32_t base[kBars];
+    uint32_t base[kBarsBig];
 #pragma unroll
-    for (int b = 0; b < kBars; ++b) base[b] = cx.cnt[b];
+    for (int b = 0; b < kBarsBig; ++b) base[b] = cx.cnt[b];
     float sre[64], sim[64];
 #pragma unroll
     for (int j = 0; j < 64; ++j) sre[j] = sim[j] = 0.f;

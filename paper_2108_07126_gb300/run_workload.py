@@ -4,7 +4,8 @@
 
 Workloads: ``rabi`` (d = 2, midpoint), ``spins`` (d = 16, GL4 Magnus), ``gradient``
 (d = 8, loss + adjoint gradient), ``dense`` (d = 128, GL4 Magnus), ``batched``
-(mixed instances, d up to 64, one persistent launch).  ``--exp chebyshev`` selects the
+(mixed instances, d up to 64, one persistent launch), ``random`` (dense random problem of
+dimension ``--dim``, two controls, midpoint, ||G|| ~ 0.3).  ``--exp chebyshev`` selects the
 paper's Chebyshev exponential, ``--traj-every n`` times the trajectory U(t_n) instead of
 U(T).  Times are CUDA events on the
 launching stream around each call, after one warm-up call.
@@ -39,7 +40,9 @@ def _time(fn, reps):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", choices=["rabi", "spins", "gradient", "dense", "batched"], default="spins")
+    ap.add_argument("--workload", choices=["rabi", "spins", "gradient", "dense", "batched", "random"],
+                    default="spins")
+    ap.add_argument("--dim", type=int, default=64, help="dimension of the random workload")
     ap.add_argument("--prec", default="fp32")
     ap.add_argument("--n-steps", type=int, default=0, help="slices (0 = the workload's default)")
     ap.add_argument("--n-inst", type=int, default=256, help="instances of the batched workload")
@@ -60,7 +63,9 @@ def main(argv=None):
         res["n_steps"] = sum(p.n_steps for p in probs)
     else:
         make = {"rabi": wl.rabi_qubit, "spins": wl.coupled_spins, "gradient": wl.gradient_qubits,
-                "dense": wl.dense_stress}[args.workload]
+                "dense": wl.dense_stress,
+                "random": lambda n_steps=4096: wl.random_problem(args.dim, 2, n_steps, "midpoint", seed=5,
+                                                                 g_norm=0.3)}[args.workload]
         prob = make(n_steps=args.n_steps) if args.n_steps else make()
         if args.exp == "chebyshev":
             prop.set_option(b.PARAMENT_OPT_EXP_METHOD, 1)

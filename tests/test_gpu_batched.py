@@ -72,17 +72,49 @@ def test_batched_fp64_matches_oracle(prop, graph, integrator):
             assert np.max(np.abs(U.cpu().numpy() - r)) <= TOL64, (p.name, rep)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp32_tc_tf32x3"])
-def test_batched_fp32_matches_oracle(prop, prec):
+@pytest.mark.parametrize("integrator", ["midpoint", "magnus4_gl2"])
+@pytest.mark.parametrize("prec", ["fp32", "fp32_tc_tf32x3", "fp32_tc_bf16x3"])
+def test_batched_fp32_matches_oracle(prop, prec, integrator):
     import torch
 
-    probs = mixed_batch("midpoint", seed=2)
+    from paper_2108_07126_gb300 import binding as b
+
+    probs = mixed_batch(integrator, seed=2) + [wl.random_problem(100, 2, 33, integrator, seed=77, g_norm=0.3),
+                                               wl.random_problem(128, 1, 20, integrator, seed=78, g_norm=0.3)]
     inst, keep, outs = prop.batch([(p.H0, p.Hk, p.c, p.dt, p.n_steps) for p in probs], prec)
-    prop.propagate_batched(inst, prec)
+    prop.propagate_batched(inst, prec, integrator)
     torch.cuda.synchronize()
     for p, U, r in zip(probs, outs, refs(probs, rounded=True)):
         err = np.max(np.abs(U.cpu().numpy().astype(np.complex128) - r))
         assert err <= 2 * tol32(p.dim, p.n_steps), (p.name, err)
+    st = prop.stats()
+    want = b.PARAMENT_BACKEND_CUDA_CORES | (0 if prec == "fp32" else b.PARAMENT_BACKEND_TCGEN05)
+    assert st["product_backends"] == want and st["device_status"] == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32_tc_tf32x3", "fp32_tc_bf16x3"])
+def test_batched_tensor_core_classes_on_cuda_cores(prop, prec):
+    """PARAMENT_OPT_BATCH_CUDA_CORE_CLASSES moves chosen dimension classes back to the CUDA cores;
+    the autotuner picks a mask and reports it."""
+    import torch
+
+    from paper_2108_07126_gb300 import binding as b
+
+    probs = mixed_batch("midpoint", seed=4) + [wl.random_problem(128, 1, 20, "midpoint", seed=79, g_norm=0.3)]
+    inst, keep, outs = prop.batch([(p.H0, p.Hk, p.c, p.dt, p.n_steps) for p in probs], prec)
+    R = refs(probs, rounded=True)
+    for mask, want in ((0b111, b.PARAMENT_BACKEND_CUDA_CORES),
+                       (0b011, b.PARAMENT_BACKEND_CUDA_CORES | b.PARAMENT_BACKEND_TCGEN05)):
+        prop.set_option(b.PARAMENT_OPT_BATCH_CUDA_CORE_CLASSES, mask)
+        prop.propagate_batched(inst, prec)
+        torch.cuda.synchronize()
+        assert prop.stats()["product_backends"] == want, mask
+        for p, U, r in zip(probs, outs, R):
+            err = np.max(np.abs(U.cpu().numpy().astype(np.complex128) - r))
+            assert err <= 2 * tol32(p.dim, p.n_steps), (mask, p.name, err)
+    leaf, items, ms, mask = prop.batch_autotune(inst, prec)
+    assert 0 <= mask <= 7 and ms > 0
+    assert prop.get_option(b.PARAMENT_OPT_BATCH_CUDA_CORE_CLASSES) == mask
 
 
 def test_batched_matches_single_calls(prop):
@@ -105,7 +137,7 @@ def test_batched_workload_sample_and_autotune(prop):
 
     probs = wl.batched_instances(n_inst=24, n_max=2e4)
     inst, keep, outs = prop.batch([(p.H0, p.Hk, p.c, p.dt, p.n_steps) for p in probs], "fp32")
-    leaf, items, ms = prop.batch_autotune(inst, "fp32")
+    leaf, items, ms, _ = prop.batch_autotune(inst, "fp32")
     assert leaf in (32, 128) and items in (8, 16, 32, 64) and ms > 0
     prop.propagate_batched(inst, "fp32")
     torch.cuda.synchronize()

@@ -264,24 +264,70 @@ def test_large_d_fp32_matches_oracle(prop, d):
     assert np.max(np.abs(U - ref32(prob))) <= tol32(d, n)
 
 
-@pytest.mark.parametrize("d", [32, 64, 128, 192])
+def run_stats(prop, prob, prec):
+    import torch
+
+    U = run(prop, prob, prec, c_dtype=torch.float32, h_dtype=torch.complex64)
+    return U, prop.stats()
+
+
+@pytest.mark.parametrize("d", [17, 32, 40, 64, 100, 128, 192])
 def test_tensor_core_tf32x3_matches_oracle(prop, d):
-    """3xTF32 tensor-core products keep FP32 accuracy."""
+    """3xTF32 tensor-core products keep FP32 accuracy; d <= 128 runs tcgen05, d > 128 mma.sync."""
+    from paper_2108_07126_gb300 import binding as b
+
     n = 301 if d <= 64 else 41
     prob = wl.random_problem(d, 3, n, "magnus4_gl2", seed=900 + d, g_norm=0.5)
-    U = run(prop, prob, "fp32_tc_tf32x3", c_dtype=__import__("torch").float32,
-            h_dtype=__import__("torch").complex64)
+    U, st = run_stats(prop, prob, "fp32_tc_tf32x3")
     assert np.max(np.abs(U - ref32(prob))) <= 2 * tol32(d, n)
+    assert st["product_backends"] == (b.PARAMENT_BACKEND_TCGEN05 if d <= 128 else b.PARAMENT_BACKEND_MMA_SYNC)
+    assert st["device_status"] == 0
 
 
-@pytest.mark.parametrize("d", [40, 64, 100, 128])
+@pytest.mark.parametrize("d", [20, 32, 40, 64, 100, 128])
 def test_tensor_core_bf16x3_matches_oracle(prop, d):
     """Split BF16x3 on tcgen05 (kind::f16, six products per real product) keeps FP32 accuracy."""
+    from paper_2108_07126_gb300 import binding as b
+
     n = 301 if d <= 64 else 41
     prob = wl.random_problem(d, 3, n, "magnus4_gl2", seed=950 + d, g_norm=0.5)
-    U = run(prop, prob, "fp32_tc_bf16x3", c_dtype=__import__("torch").float32,
-            h_dtype=__import__("torch").complex64)
+    U, st = run_stats(prop, prob, "fp32_tc_bf16x3")
     assert np.max(np.abs(U - ref32(prob))) <= 2 * tol32(d, n)
+    assert st["product_backends"] == b.PARAMENT_BACKEND_TCGEN05
+    assert st["device_status"] == 0
+
+
+@pytest.mark.parametrize("integrator", ["midpoint", "magnus4_simpson"])
+@pytest.mark.parametrize("d,prec", [(32, "fp32_tc_tf32x3"), (64, "fp32_tc_bf16x3"), (64, "fp32_tc_tf32x3")])
+def test_tensor_core_small_d_integrators(prop, integrator, d, prec):
+    """The shared-memory tcgen05 body (d = 17..64) with the other two integrators and a norm range
+    that needs squarings."""
+    prob = wl.random_problem(d, 2, 257, integrator, seed=970 + d, g_norm=2.5)
+    U, st = run_stats(prop, prob, prec)
+    assert st["max_squarings"] >= 1
+    assert np.max(np.abs(U - ref32(prob))) <= 2 * tol32(d, prob.n_steps)
+
+
+@pytest.mark.parametrize("grid", [1, 3, 152, 304])
+def test_tensor_core_small_d_tree_shapes(prop, grid):
+    """Leaf lengths from 1 to the whole run: the same U(T) up to FP32 rounding."""
+    from paper_2108_07126_gb300 import binding as b
+
+    prob = wl.random_problem(48, 2, 400, "magnus4_gl2", seed=981, g_norm=0.5)
+    prop.set_option(b.PARAMENT_OPT_GRID_BLOCKS, grid)
+    U, st = run_stats(prop, prob, "fp32_tc_tf32x3")
+    assert st["grid_blocks"] == min(grid, prob.n_steps)
+    assert np.max(np.abs(U - ref32(prob))) <= 2 * tol32(48, prob.n_steps)
+
+
+def test_product_backends_reported(prop):
+    """parament_stats names the code that ran the products: CUDA cores for FP64, FP32 and d <= 16."""
+    from paper_2108_07126_gb300 import binding as b
+
+    for d, prec in ((8, "fp32"), (8, "fp64"), (64, "fp32"), (64, "fp64"), (128, "fp32")):
+        prob = wl.random_problem(d, 2, 20, "midpoint", seed=990 + d, g_norm=0.3)
+        run(prop, prob, prec)
+        assert prop.stats()["product_backends"] == b.PARAMENT_BACKEND_CUDA_CORES, (d, prec)
 
 
 def test_tensor_core_modes_rejected_where_not_built(prop, torch):
@@ -457,7 +503,8 @@ def test_chebyshev_large_d_fp64_matches_oracle(prop, integrator, d):
     assert st["exp_products"] == st["max_degree"] * n and st["max_squarings"] == 0
 
 
-@pytest.mark.parametrize("d,prec", [(32, "fp32"), (64, "fp32"), (128, "fp32"), (128, "fp32_tc_tf32x3")])
+@pytest.mark.parametrize("d,prec", [(32, "fp32"), (64, "fp32"), (128, "fp32"), (128, "fp32_tc_tf32x3"),
+                                    (32, "fp32_tc_tf32x3"), (64, "fp32_tc_bf16x3")])
 def test_chebyshev_large_d_fp32_matches_oracle(prop, d, prec):
     import torch
 
