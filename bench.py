@@ -34,7 +34,6 @@ if ROOT not in sys.path:
 
 METRIC = "time steps/sec to full U(T), by dim, vs plain FP64 GPU path at stated error"
 UNIT = "time steps/s"
-FP32_PEAK_TFLOPS_NOTE = "152 SMs x 128 FP32 lanes x 2 flop/FMA x 2.07 GHz max SM clock"
 SM_COUNT, FP32_LANES, FP64_FMA_PER_SM_CLK = 152, 128, 2
 L2_FLUSH_BYTES = 256 << 20
 # dram__bytes_read.sum + dram__bytes_write.sum of fused_small_kernel<float, 16, GL4> from one ncu capture of
@@ -51,6 +50,36 @@ def _measured_peaks() -> dict:
 
 
 PEAKS = _measured_peaks()
+# rates measured on this GPU by parament_measure_peaks (filled once per run, rank 0)
+MEASURED = {}
+
+
+def measure_peaks(b, device: int) -> dict:
+    MEASURED.update(b.parament_measure_peaks(device))
+    return dict(MEASURED)
+
+
+def roofline_alu(achieved: float, pipe: str) -> dict:
+    """Roofline of a CUDA-core kernel against the measured FMA rate of its pipe (fp32 / fp64)."""
+    pk = MEASURED.get(f"{pipe}_tflops_max_clock") or MEASURED.get(f"{pipe}_tflops")
+    if pk:
+        note = (f"measured {pipe.upper()} FMA rate (parament_measure_peaks: independent FMA chains filling every "
+                f"SM, flops per SM clock cycle x the {MEASURED.get('max_sm_clock_mhz', 0):.0f} MHz maximum clock)")
+    else:
+        per_clk = FP32_LANES if pipe == "fp32" else FP64_FMA_PER_SM_CLK
+        pk = SM_COUNT * per_clk * 2 * 2.07e9 / 1e12
+        note = "derived from unit counts (measurement unavailable)"
+    return {"bound": "alu", "pipe": pipe, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+            "frac": achieved / pk, "peak_note": note}
+
+
+def tensor_peak(fmt: str) -> tuple[float, str]:
+    """Dense tcgen05 rate of the format (tf32 / bf16): measured here, else the pool's cuBLAS bf16 figure."""
+    pk = MEASURED.get(f"{fmt}_tflops")
+    if pk:
+        return pk, f"measured dense tcgen05 {fmt.upper()} rate (parament_measure_peaks: M128 N256 MMA stream per SM)"
+    bf = PEAKS.get("bf16_tflops", 1900.0)
+    return (bf * 1.1 / 2.25 if fmt == "tf32" else bf), "cuBLAS bf16 burst of MEASURED_PEAKS.json (TF32 x 1.1 / 2.25)"
 TRAFFIC_NOTE = "ncu capture of 2^18 slices (16.92 MB) scaled to the launch; algorithmic 64 B per slice"
 
 
@@ -273,6 +302,19 @@ def time_launches(torch, fn, steps, warmup, flush):
     return [a.elapsed_time(b) for a, b in evs]
 
 
+def batched_sample(probs):
+    """Instances of the batched sweep compared with the oracle: the longest of every dimension and
+    eight drawn with a fixed seed."""
+    import numpy as np
+
+    picked = set()
+    for d in sorted({p.dim for p in probs}):
+        picked.add(max((i for i, p in enumerate(probs) if p.dim == d), key=lambda i: probs[i].n_steps))
+    rng = np.random.default_rng(20210816)
+    picked.update(int(i) for i in rng.choice(len(probs), 8, replace=False))
+    return sorted(picked)
+
+
 def secondary_workloads(torch, b, wl, dev, flush, steps=10, warmup=3):
     """Rabi qubit (d = 2, N = 2^14, latency-bound) and the optimal-control gradient (d = 8, N = 65536)."""
     import numpy as np
@@ -313,16 +355,27 @@ def secondary_workloads(torch, b, wl, dev, flush, steps=10, warmup=3):
             "grad_max_rel_err_vs_oracle": float(np.max(np.abs(g - g_ref)) / np.max(np.abs(g_ref))),
             "launches_per_step": 5, "timing": "host wall clock incl. the loss read-back"}
     # ---- batched sweep: 256 instances, d in {2..64}, N log-uniform in [1e3, 1e5]
+    from oracle.parallel import propagate_parallel
+
     probs = wl.batched_instances()
     total_steps = sum(p.n_steps for p in probs)
-    inst32, keep32, outs32 = prop.batch([(p.H0, p.Hk, p.c, p.dt, p.n_steps) for p in probs], "fp32")
-    leaf, items, tune_ms, _ = prop.batch_autotune(inst32, "fp32")
-    per = time_launches(torch, lambda: prop.propagate_batched(inst32, "fp32"), 5, 2, flush)
-    ms32 = statistics.mean(per)
-    inst_tc, keep_tc, outs_tc = prop.batch([(p.H0, p.Hk, p.c, p.dt, p.n_steps) for p in probs], "fp32_tc_tf32x3")
-    prop.batch_autotune(inst_tc, "fp32_tc_tf32x3")
-    per_tc = time_launches(torch, lambda: prop.propagate_batched(inst_tc, "fp32_tc_tf32x3"), 5, 2, flush)
-    ms_tc = statistics.mean(per_tc)
+    sample = batched_sample(probs)
+    R_sample = {i: propagate_parallel(probs[i].H0, probs[i].Hk, probs[i].c, probs[i].dt, probs[i].integrator)
+                for i in sample}
+    forms = {}
+    for prec in ("fp32", "fp32_tc_tf32x3", "fp32_tc_bf16x3"):
+        inst, keep, outs = prop.batch([(p.H0, p.Hk, p.c, p.dt, p.n_steps) for p in probs], prec)
+        leaf, items, tune_ms, cuda_mask = prop.batch_autotune(inst, prec)
+        per = time_launches(torch, lambda: prop.propagate_batched(inst, prec), 5, 2, flush)
+        ms = statistics.mean(per)
+        Us = [U.cpu().numpy().astype(np.complex128) for U in outs]
+        forms[prec] = {"steps_per_s": total_steps / (ms * 1e-3), "ms": ms, "cuda_graph": True,
+                       "autotuned": {"leaf_steps": leaf, "items_per_sm": items,
+                                     "cuda_core_classes": cuda_mask},
+                       "product_backends": prop.stats()["product_backends"],
+                       "max_abs_err_vs_oracle_sample": max(float(np.max(np.abs(Us[i] - R_sample[i])))
+                                                           for i in sample), "U": Us}
+        del keep, outs
     # plain FP64 GPU path: one propagate per instance
     U64 = []
     t0 = torch.cuda.Event(enable_timing=True)
@@ -336,62 +389,66 @@ def secondary_workloads(torch, b, wl, dev, flush, steps=10, warmup=3):
     t1.record()
     torch.cuda.synchronize()
     ms64 = t0.elapsed_time(t1)
-    err32 = max(float(torch.max(torch.abs(a.to(torch.complex128) - b)).item()) for a, b in zip(outs32, U64))
-    err_tc = max(float(torch.max(torch.abs(a.to(torch.complex128) - b)).item()) for a, b in zip(outs_tc, U64))
+    U64 = [U.cpu().numpy() for U in U64]
+    err64_sample = max(float(np.max(np.abs(U64[i] - R_sample[i]))) for i in sample)
+    for prec, f in forms.items():
+        f["max_abs_err_vs_fp64_gpu"] = max(float(np.max(np.abs(a - b))) for a, b in zip(f.pop("U"), U64))
     out["batched_256_instances_d2to64"] = {
         "total_steps": total_steps, "n_instances": len(probs),
-        "fp32_batched": {"steps_per_s": total_steps / (ms32 * 1e-3), "ms": ms32, "launches": 2,
-                         "autotuned": {"leaf_steps": leaf, "items_per_sm": items}, "cuda_graph": True,
-                         "max_abs_err_vs_fp64_gpu": err32},
-        "fp32_tc_tf32x3_batched": {"steps_per_s": total_steps / (ms_tc * 1e-3), "ms": ms_tc,
-                                   "max_abs_err_vs_fp64_gpu": err_tc},
+        "oracle_sample": f"{len(sample)} instances: the longest of each dimension and 8 drawn with seed 20210816",
+        "fp32_batched": forms["fp32"], "fp32_tc_tf32x3_batched": forms["fp32_tc_tf32x3"],
+        "fp32_tc_bf16x3_batched": forms["fp32_tc_bf16x3"],
         "fp64_gpu_per_instance_loop": {"steps_per_s": total_steps / (ms64 * 1e-3), "ms": ms64,
+                                       "max_abs_err_vs_oracle_sample": err64_sample,
                                        "note": "set_hamiltonians + set_controls + propagate per instance, "
                                                "the set-up synchronises"},
-        "speedup_fp32_batched_vs_fp64_loop": ms64 / ms32}
-    del keep32, keep_tc, outs32, outs_tc, U64
+        "speedup_fp32_batched_vs_fp64_loop": ms64 / forms["fp32"]["ms"]}
+    del U64
 
     # ---- dense precision stress: d = 128, GL4, N = 2^16 (FP64 timed on 2^12 slices)
     prob = wl.dense_stress()
     small = wl.dense_stress(n_steps=1 << 12)
+    R = propagate_parallel(prob.H0, prob.Hk, prob.c, prob.dt, prob.integrator)
     res = {}
     for name, prb in (("full", prob), ("small", small)):
-        for prec in ("fp32", "fp32_tc_tf32x3", "fp32_tc_bf16x3") + (("fp64",) if name == "small" else ()):
+        for prec in ("fp32", "fp32_tc_tf32x3", "fp32_tc_bf16x3", "fp64"):
+            if name == "small" and prec != "fp64":
+                continue
             cdt = torch.complex128 if prec == "fp64" else torch.complex64
             rdt = torch.float64 if prec == "fp64" else torch.float32
             prop.set_hamiltonians(torch.as_tensor(prb.H0).to(cdt), torch.as_tensor(prb.Hk).to(cdt), prb.integrator)
             prop.set_controls(torch.as_tensor(prb.c).to(rdt).to(dev), prb.dt, prb.n_steps)
             U = torch.empty(128, 128, dtype=cdt, device=dev)
-            per = time_launches(torch, lambda: prop.propagate(prec, out=U), 3 if prec != "fp64" else 1, 1, flush)
+            if name == "full" and prec == "fp64":  # one launch for the error (about 9 s)
+                prop.propagate(prec, out=U)
+                torch.cuda.synchronize()
+                per = [float("nan")]
+            else:
+                per = time_launches(torch, lambda: prop.propagate(prec, out=U), 3 if prec != "fp64" else 1, 1, flush)
             st = prop.stats()
             res[(name, prec)] = (statistics.mean(per), U.cpu().numpy().astype(np.complex128), st)
-    U64s = res[("small", "fp64")][1]
     d128 = {}
     for prec in ("fp32", "fp32_tc_tf32x3", "fp32_tc_bf16x3"):
-        ms, _, st = res[("full", prec)]
+        ms, U, st = res[("full", prec)]
         fl = flops_per_launch(st)
-        d128[prec] = {"steps_per_s": prob.n_steps / (ms * 1e-3), "ms": ms, "algorithmic_tflops": fl / (ms * 1e-3) / 1e12,
-                      "max_abs_err_vs_fp64_gpu_N4096": float(np.max(np.abs(res[("small", prec)][1] - U64s)))}
-    # tcgen05 products: three TF32 MMAs per real product (hi hi + hi lo + lo hi), 8 d^3 flops per
-    # complex product; TF32 peak = measured bf16 peak x the nominal TF32 / bf16 ratio (1.1 / 2.25)
-    st = res[("full", "fp32_tc_tf32x3")][2]
-    n_prod = st["exp_products"] + st["tree_products"] + 2 * st["grid_blocks"]  # + Newton-Schulz step per leaf
-    tf32_peak = PEAKS.get("bf16_tflops", 1900.0) * 1.1 / 2.25
-    ach = 3.0 * 8.0 * 128 ** 3 * n_prod / (res[("full", "fp32_tc_tf32x3")][0] * 1e-3) / 1e12
-    d128["fp32_tc_tf32x3"]["roofline"] = {"bound": "tensor", "achieved": ach, "peak": tf32_peak, "unit": "TFLOP/s",
-                                           "frac": ach / tf32_peak, "kernel": "large_kernel<float, 128, GL4, tcgen05>",
-                                           "peak_note": "TF32 = measured bf16 burst x 1.1 / 2.25 (of measured)"}
-    # split BF16x3: six BF16 MMAs per real product (b0 b0, b0 b1, b1 b0, b0 b2, b1 b1, b2 b0)
-    st = res[("full", "fp32_tc_bf16x3")][2]
-    n_prod = st["exp_products"] + st["tree_products"] + 2 * st["grid_blocks"]
-    bf16_peak = PEAKS.get("bf16_tflops", 1900.0)
-    ach = 6.0 * 8.0 * 128 ** 3 * n_prod / (res[("full", "fp32_tc_bf16x3")][0] * 1e-3) / 1e12
-    d128["fp32_tc_bf16x3"]["roofline"] = {"bound": "tensor", "achieved": ach, "peak": bf16_peak, "unit": "TFLOP/s",
-                                           "frac": ach / bf16_peak, "kernel": "large_kernel<float, 128, GL4, tcgen05 bf16>",
-                                           "peak_note": "measured bf16 burst (of measured)"}
+        d128[prec] = {"steps_per_s": prob.n_steps / (ms * 1e-3), "ms": ms,
+                      "algorithmic_tflops": fl / (ms * 1e-3) / 1e12,
+                      "product_backends": st["product_backends"],
+                      "max_abs_err_vs_oracle": float(np.max(np.abs(U - R)))}
+    d128["fp32"]["roofline"] = roofline_alu(d128["fp32"]["algorithmic_tflops"], "fp32")
+    # tcgen05 products: the method's 8 d^3 flops per complex product against the pipe's peak, and
+    # the tensor pipe's own work (3 TF32 or 6 BF16 MMA flops per real flop) as utilisation
+    for prec, fmt, mult in (("fp32_tc_tf32x3", "tf32", 3.0), ("fp32_tc_bf16x3", "bf16", 6.0)):
+        ach = d128[prec]["algorithmic_tflops"]
+        pk, note = tensor_peak(fmt)
+        d128[prec]["roofline"] = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                                  "frac": ach / pk, "tensor_utilisation": mult * ach / pk,
+                                  "kernel": f"large_kernel<float, 128, GL4, tcgen05 {fmt}>", "peak_note": note}
     ms, _, st = res[("small", "fp64")]
     d128["fp64"] = {"steps_per_s": small.n_steps / (ms * 1e-3), "ms_N4096": ms,
-                    "algorithmic_tflops": flops_per_launch(st) / (ms * 1e-3) / 1e12}
+                    "algorithmic_tflops": flops_per_launch(st) / (ms * 1e-3) / 1e12,
+                    "max_abs_err_vs_oracle": float(np.max(np.abs(res[("full", "fp64")][1] - R)))}
+    d128["fp64"]["roofline"] = roofline_alu(d128["fp64"]["algorithmic_tflops"], "fp64")
     d128["speedup_tf32x3_vs_fp64"] = d128["fp32_tc_tf32x3"]["steps_per_s"] / d128["fp64"]["steps_per_s"]
     out["dense_stress_d128_magnus4_gl2_N65536"] = d128
     prop.close()
@@ -447,6 +504,14 @@ def run_ours(args):
     U64h = U64.cpu().numpy()
     err32 = float(np.max(np.abs(U32h - U64h)))
     unit_err = float(np.max(np.abs(U64h.conj().T @ U64h - np.eye(16))))
+    # both paths against the FP64 oracle on the full workload (exact inputs), rank 0 only
+    err32_oracle = err64_oracle = None
+    if rank == 0:
+        from oracle.parallel import propagate_parallel
+
+        R = propagate_parallel(prob.H0, prob.Hk, prob.c, prob.dt, prob.integrator)
+        err32_oracle = float(np.max(np.abs(U32h - R)))
+        err64_oracle = float(np.max(np.abs(U64h - R)))
 
     # ---- end to end through the C ABI with host buffers (pinned controls in, host U out)
     c_host = torch.as_tensor(prob.c).to(torch.float32).pin_memory()
@@ -463,6 +528,10 @@ def run_ours(args):
             e2e_times.append(t1 - t0)
     e2e_s = max_over_ranks(statistics.mean(e2e_times), world, dev)
     prop.close()
+
+    # ---- measured pipe rates for the rooflines (rank 0, outside the timed regions)
+    if rank == 0:
+        measure_peaks(b, local)
 
     # ---- secondary workloads (reported beside the headline, not part of `value`)
     extra = {}
@@ -482,10 +551,10 @@ def run_ours(args):
         return
     fl32 = flops_per_launch(st32)
     fl64 = flops_per_launch(st64)
-    peak32 = SM_COUNT * FP32_LANES * 2 * 2.07e9 / 1e12
-    peak64 = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * 2.07e9 / 1e12
     ach32 = fl32 / (statistics.mean(per32) * 1e-3) / 1e12
     ach64 = fl64 / (statistics.mean(per64) * 1e-3) / 1e12
+    roof32 = roofline_alu(ach32, "fp32")
+    roof64 = roofline_alu(ach64, "fp64")
     value = world * N / (ms32 * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -493,21 +562,22 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": dict(workload_config(N, "fp32"), parallelism=("replicas" if world > 1 else "single"),
                        n_basis_kept=st32["n_basis"]),
+        "max_abs_err_vs_oracle": err32_oracle,
         "fp64_gpu": {"value": world * N / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64,
-                     "steps": args.fp64_steps, "max_abs_err_vs_oracle_bound": 1e-11,
+                     "steps": args.fp64_steps, "max_abs_err_vs_oracle": err64_oracle,
+                     "max_abs_err_vs_oracle_bound": 1e-11,
                      "unitarity_err": unit_err, "exp_products": st64["exp_products"],
                      "max_degree": st64["max_degree"], "max_squarings": st64["max_squarings"],
-                     "roofline": {"bound": "alu", "pipe": "fp64", "achieved": ach64, "peak": peak64,
-                                  "unit": "TFLOP/s", "frac": ach64 / peak64}},
+                     "roofline": roof64},
         "speedup_vs_fp64_gpu": ms64 / ms32,
         "max_abs_err_vs_fp64_gpu": err32,
         "kernel": {"grid_blocks": st32["grid_blocks"], "block_threads": st32["block_threads"],
                    "leaves": st32["leaves"], "exp_products": st32["exp_products"],
                    "tree_products": st32["tree_products"], "max_degree": st32["max_degree"],
                    "max_squarings": st32["max_squarings"], "flops_per_launch": fl32},
-        "roofline": {"bound": "alu", "achieved": ach32, "peak": peak32, "unit": "TFLOP/s", "frac": ach32 / peak32,
-                     "traffic": TRAFFIC_BYTES_PER_SLICE * N, "traffic_note": TRAFFIC_NOTE,
-                     "peak_note": FP32_PEAK_TFLOPS_NOTE},
+        "roofline": dict(roof32, traffic=TRAFFIC_BYTES_PER_SLICE * N, traffic_note=TRAFFIC_NOTE),
+        "peaks": dict(MEASURED, bf16_cublas_tflops_pool=PEAKS.get("bf16_tflops"),
+                      note="measured by parament_measure_peaks in this run, after the timed region"),
         "cpu_baseline": cpu,
         "e2e": {"value": world * N / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(c_host.numel() * 4),
                 "d2h_bytes_per_step": int(U_host.nbytes)},

@@ -421,6 +421,38 @@ int parament_chebyshev_degree(double half_width, double u);
    Chebyshev coefficients a_k = (-i)^k J_k(beta) of Sec. 2.1; host-only, the kernels use the same code. */
 int parament_bessel_j(int n, double x, double *out);
 
+/*
+ * --- Measured peaks ----------------------------------------------------------
+ * Not part of the paper's method: a measurement helper for reporting rooflines.
+ * Times, on device `device` and stream `cuda_stream` (NULL = legacy default),
+ * the rates the propagator's kernels are bound by, in TFLOP/s (2 flops per
+ * multiply-add):
+ *   fp32_tflops / fp64_tflops: independent fused multiply-add chains on the CUDA
+ *     cores over a grid that fills every SM (the best of a few chain counts and
+ *     occupancies); the *_max_clock figures count flops per SM clock cycle
+ *     (clock64) instead of per second and scale them to the maximum SM clock, so
+ *     they do not depend on the clock the GPU ran during the measurement;
+ *   tf32_tflops / bf16_tflops: a stream of dense tcgen05 MMAs (M = 128, N = 256,
+ *     K = 8 TF32 or 16 BF16, FP32 accumulation in tensor memory) issued by one
+ *     thread per SM on operands in shared memory.
+ * Each figure is the median of three timed launches (CUDA events) after a
+ * warm-up launch, about 2 s in all; the call waits for the stream.  Allocates
+ * two small device buffers (released before it returns).  Errors: CUDA,
+ * TIMEOUT (a bounded wait on the tensor cores gave up; the figures are invalid).
+ */
+typedef struct {
+    double fp32_tflops;
+    double fp64_tflops;
+    double tf32_tflops;
+    double bf16_tflops;
+    int32_t sm_count;
+    int32_t reserved;
+    double max_sm_clock_mhz;      /* the device's reported maximum SM clock */
+    double fp32_tflops_max_clock; /* flops per SM clock cycle (clock64) x the maximum SM clock */
+    double fp64_tflops_max_clock;
+} parament_peaks;
+int parament_measure_peaks(int device, void *cuda_stream, parament_peaks *out);
+
 /* Static text for a status code. */
 const char *parament_status_string(int status);
 

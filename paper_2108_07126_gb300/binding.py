@@ -101,6 +101,20 @@ class parament_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_ if not name.startswith("reserved")}
 
 
+class parament_peaks(ctypes.Structure):
+    _fields_ = [
+        ("fp32_tflops", ctypes.c_double),
+        ("fp64_tflops", ctypes.c_double),
+        ("tf32_tflops", ctypes.c_double),
+        ("bf16_tflops", ctypes.c_double),
+        ("sm_count", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("max_sm_clock_mhz", ctypes.c_double),
+        ("fp32_tflops_max_clock", ctypes.c_double),
+        ("fp64_tflops_max_clock", ctypes.c_double),
+    ]
+
+
 class parament_instance(ctypes.Structure):
     _fields_ = [
         ("dim", ctypes.c_int),
@@ -141,6 +155,7 @@ _SIGS = {
                                  ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                  ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_uint32)], ctypes.c_int),
+    "parament_measure_peaks": ([ctypes.c_int, _vp, ctypes.POINTER(parament_peaks)], ctypes.c_int),
     "parament_chebyshev_theta": ([ctypes.c_int, ctypes.c_double], ctypes.c_double),
     "parament_chebyshev_degree": ([ctypes.c_double, ctypes.c_double], ctypes.c_int),
     "parament_bessel_j": ([ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -279,6 +294,13 @@ def parament_batch_autotune(ctx, inst: list, dtype: int, cdtype: int, integrator
     _check(_lib.parament_batch_autotune(ctx, arr, len(inst), int(dtype), int(cdtype), int(integrator), int(prec),
                                         ctypes.byref(l), ctypes.byref(i), ctypes.byref(ms), ctypes.byref(m)), ctx)
     return l.value, i.value, ms.value, m.value
+
+
+def parament_measure_peaks(device: int = 0, stream: int | None = None) -> dict:
+    """Measured FP32 / FP64 FMA and TF32 / BF16 tcgen05 rates of the device (TFLOP/s)."""
+    pk = parament_peaks()
+    _check(_lib.parament_measure_peaks(int(device), stream or None, ctypes.byref(pk)))
+    return {name: getattr(pk, name) for name, _ in pk._fields_ if name != "reserved"}
 
 
 def parament_chebyshev_theta(m: int, u: float) -> float:

@@ -26,6 +26,7 @@ SOURCES = [
     "pm_fused_d8.cu",
     "pm_fused_d16.cu",
     "pm_noalloc.cu",
+    "pm_peaks.cu",
     "pm_grad_d2.cu",
     "pm_grad_d4.cu",
     "pm_grad_d8.cu",

@@ -1,21 +1,14 @@
 """Batched propagation of instances with uneven dimension and step count (one persistent launch)."""
 
-import math
-
 import numpy as np
 import pytest
 
 import oracle
 from paper_2108_07126_gb300 import workloads as wl
+from tolerances import TOL64, U32, check, tol32, tol_tc  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
-TOL64 = 1e-11
-U32 = 2.0 ** -24
-
-
-def tol32(d, n):
-    return 20.0 * U32 * max(d, 2) * math.sqrt(max(n, 1)) + 1e-6
 
 
 @pytest.fixture()
@@ -86,7 +79,7 @@ def test_batched_fp32_matches_oracle(prop, prec, integrator):
     torch.cuda.synchronize()
     for p, U, r in zip(probs, outs, refs(probs, rounded=True)):
         err = np.max(np.abs(U.cpu().numpy().astype(np.complex128) - r))
-        assert err <= 2 * tol32(p.dim, p.n_steps), (p.name, err)
+        check(err, (tol32 if prec == "fp32" else tol_tc)(p.dim, p.n_steps), (p.name, err))
     st = prop.stats()
     want = b.PARAMENT_BACKEND_CUDA_CORES | (0 if prec == "fp32" else b.PARAMENT_BACKEND_TCGEN05)
     assert st["product_backends"] == want and st["device_status"] == 0
@@ -111,7 +104,7 @@ def test_batched_tensor_core_classes_on_cuda_cores(prop, prec):
         assert prop.stats()["product_backends"] == want, mask
         for p, U, r in zip(probs, outs, R):
             err = np.max(np.abs(U.cpu().numpy().astype(np.complex128) - r))
-            assert err <= 2 * tol32(p.dim, p.n_steps), (mask, p.name, err)
+            check(err, tol_tc(p.dim, p.n_steps), (mask, p.name, err))
     leaf, items, ms, mask = prop.batch_autotune(inst, prec)
     assert 0 <= mask <= 7 and ms > 0
     assert prop.get_option(b.PARAMENT_OPT_BATCH_CUDA_CORE_CLASSES) == mask
@@ -143,7 +136,7 @@ def test_batched_workload_sample_and_autotune(prop):
     torch.cuda.synchronize()
     for p, U, r in zip(probs, outs, refs(probs, rounded=True)):
         err = np.max(np.abs(U.cpu().numpy().astype(np.complex128) - r))
-        assert err <= 2 * tol32(p.dim, p.n_steps), (p.name, err)
+        check(err, tol32(p.dim, p.n_steps), (p.name, err))
 
 
 def test_batched_workload_full_size(prop):
@@ -160,14 +153,14 @@ def test_batched_workload_full_size(prop):
     Us = [U.cpu().numpy().astype(np.complex128) for U in outs]
     for p, U in zip(probs, Us):
         unit = np.max(np.abs(U.conj().T @ U - np.eye(p.dim)))
-        assert unit <= tol32(p.dim, p.n_steps), (p.name, unit)
+        check(unit, tol32(p.dim, p.n_steps), (p.name, unit))
     picked = []
     for d in sorted({p.dim for p in probs}):
         same = sorted((i for i, p in enumerate(probs) if p.dim == d), key=lambda i: probs[i].n_steps)
         picked += same[:2]
     for i, r in zip(picked, refs([probs[i] for i in picked], rounded=True)):
         err = np.max(np.abs(Us[i] - r))
-        assert err <= 2 * tol32(probs[i].dim, probs[i].n_steps), (probs[i].name, err)
+        check(err, tol32(probs[i].dim, probs[i].n_steps), (probs[i].name, err))
 
 
 def test_batched_rejects_host_pointers(prop):

@@ -5,8 +5,9 @@ FP64: the adjoint gradient agrees with the oracle to 1e-9 relative to max |g|
 (the two use different exponential and Frechet-derivative algorithms; the bound
 leaves room for N accumulated rounding errors of ~1e-15), and with central
 finite differences of the GPU forward (h = 1e-6) to 1e-6 relative, as the
-optimal-control workload requires.  FP32: the measured error is reported; the
-test bound 3e-3 relative follows the FP32 forward error growth (20 u d sqrt(N)).
+optimal-control workload requires.  FP32: relative to max |g|, the gradient's error grows like
+the forward FP32 error (a random walk of slice rounding, u sqrt(N)); the bound GRAD32_REL is a
+few times the measured error (4.8e-5 at N = 65 536 with exact inputs).
 """
 
 import math
@@ -16,8 +17,11 @@ import pytest
 
 import oracle
 from paper_2108_07126_gb300 import workloads as wl
+from tolerances import check
 
 pytestmark = pytest.mark.gpu
+
+GRAD32_REL = 2e-4  # FP32 gradient vs the oracle, relative to max |g|
 
 
 @pytest.fixture()
@@ -110,8 +114,8 @@ def test_fp32_gradient_error(prop):
     loss, grad, U = gpu_grad(prop, prob, prob.V, "fp32")
     l_ref, g_ref, _ = oracle.loss_and_gradient(prob.H0, prob.Hk, prob.c, prob.dt, prob.V)
     rel = np.max(np.abs(grad - g_ref)) / np.max(np.abs(g_ref))
-    assert rel <= 3e-3, rel
-    assert abs(loss - l_ref) <= 1e-3
+    check(rel, GRAD32_REL, "fp32 gradient, relative")
+    check(abs(loss - l_ref), 4e-6, "fp32 loss")
 
 
 def test_gradient_invariants(prop):
@@ -151,7 +155,7 @@ def test_fp32_magnus_gradient_error(prop, integrator):
     loss, grad, _ = gpu_grad(prop, prob, V, "fp32", integrator=integrator)
     l_ref, g_ref, _ = oracle.loss_and_gradient(prob.H0, prob.Hk, prob.c, prob.dt, V, integrator)
     rel = np.max(np.abs(grad - g_ref)) / np.max(np.abs(g_ref))
-    assert rel <= 3e-3, rel
+    check(rel, GRAD32_REL, ("fp32 Magnus gradient, relative", integrator))
 
 
 def test_magnus_gradient_checkpoints_agree(prop):

@@ -459,3 +459,15 @@ def test_planted_gradient_without_conj_fails_fd(monkeypatch):
     g_ok = np.array([grad_ok[k, j] for (k, j) in entries])
     assert np.max(np.abs(g_ok - fd)) <= 1e-6 * np.max(np.abs(fd))
     assert np.max(np.abs(g_bad - fd)) > 1e-3 * np.max(np.abs(fd))
+
+
+@pytest.mark.parametrize("integrator", ["midpoint", "magnus4_gl2", "magnus4_simpson"])
+def test_parallel_oracle_equals_single_process(integrator):
+    """The multi-process oracle (contiguous slice ranges, partial products in time order) gives the
+    single-process oracle's U(T) up to FP64 rounding, for every integrator's sample layout."""
+    from oracle.parallel import propagate_parallel
+
+    prob = wl.random_problem(5, 2, 301, integrator, seed=1234, g_norm=0.4)
+    U1 = oracle.propagate(prob.H0, prob.Hk, prob.c, prob.dt, prob.integrator)
+    U4 = propagate_parallel(prob.H0, prob.Hk, prob.c, prob.dt, prob.integrator, workers=4)
+    assert np.max(np.abs(U1 - U4)) <= 1e-13

@@ -14,22 +14,15 @@ This file is collected last on purpose: if it fails, a run that stops at the
 first failure has already run every other test.
 """
 
-import math
-
 import numpy as np
 import pytest
 
 import oracle
 from paper_2108_07126_gb300 import workloads as wl
+from tolerances import TOL64, U32, check, tol32  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
-TOL64 = 1e-11
-U32 = 2.0 ** -24
-
-
-def tol32(d, n):
-    return 20.0 * U32 * max(d, 2) * math.sqrt(max(n, 1)) + 1e-6
 
 
 CASES = [
@@ -107,7 +100,7 @@ def test_noalloc_matches_context_entry_point(name, make, prec):
         U, status = _noalloc(prob, prec, H0, Hk, c, dtype, cdtype, cdt)
         assert status == 0, (name, call, status)
         err = np.max(np.abs(U - U_ref))
-        assert err <= tol, (name, prec, call, err)
+        check(err, tol, (name, prec, call))
         if prob.n_steps == 0:
             assert np.array_equal(U, np.eye(d)), (name, call)
 
