@@ -97,6 +97,10 @@ def parse_args():
     ap.add_argument("--scaling", action="store_true",
                     help="re-run the paper's performance experiments (run time vs d and vs N, CPU crossover) "
                          "instead of the benchmark line")
+    ap.add_argument("--scaling-out", default=os.path.join(ROOT, "results", "scaling_sec5.jsonl"),
+                    help="file that --scaling writes its JSON lines to (replaced)")
+    ap.add_argument("--scaling-report", action="store_true",
+                    help="print the markdown tables of a --scaling record (--scaling-out) and exit")
     return ap.parse_args()
 
 
@@ -625,6 +629,18 @@ def run_scaling(args):
     prop = b.Propagator(0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2, written between timed calls
     results = {"e1": [], "e3_gpu": [], "e3_cpu": []}
+    os.makedirs(os.path.dirname(os.path.abspath(args.scaling_out)), exist_ok=True)
+    record = open(args.scaling_out, "w")
+
+    def emit(kind, row):
+        line = json.dumps({kind: row})
+        record.write(line + "\n")
+        record.flush()
+        print(line, flush=True)
+
+    emit("meta", {"gpu": torch.cuda.get_device_name(dev), "torch": torch.__version__,
+                  "input": "random_problem(d, K=2, N, midpoint, g_norm=0.3): GUE drift, two GUE controls, "
+                           "Gaussian samples, seed 20210816 + d"})
 
     def problem(d, n):
         return wl.random_problem(d, 2, n, "midpoint", seed=20210816 + d, g_norm=0.3)
@@ -637,22 +653,32 @@ def run_scaling(args):
             prop.set_controls(torch.as_tensor(prob.c).to(rdt).to(dev), prob.dt, prob.n_steps)
         return cdt
 
-    # ---- E1: run time vs d at 80 000 time steps
+    # ---- E1: run time vs d at 80 000 time steps (every run on the full 80 000 steps; calls of
+    #      more than ~5 s are timed once after a short warm-up call)
     n1 = 80000
-    for prec in ("fp32", "fp64"):
+    dims = (2, 4, 8, 12, 16, 24, 32, 40, 48, 64, 96, 128, 160, 192)
+    for prec in ("fp32", "fp64", "fp32_tc_tf32x3"):
         rate = None
-        for d in (2, 4, 8, 12, 16, 24, 32, 40, 48, 64, 96, 128, 160, 192):
-            n = n1 if (rate is None or n1 / rate < 10.0) else max(256, int(2.0 * rate))
-            prob = problem(d, n)
-            cdt = load(prob, prec)
+        for d in dims:
+            if prec == "fp32_tc_tf32x3" and d <= 16:
+                continue
+            prob = problem(d, n1)
+            cdt = load(prob, "fp64" if prec == "fp64" else "fp32")
             U = torch.empty(d, d, dtype=cdt, device=dev)
-            per = time_launches(torch, lambda: prop.propagate(prec, out=U), 3, 1, flush)
+            if rate is not None and n1 / rate > 5.0:
+                prop.propagate(prec, out=U)  # warm-up (kernels loaded, workspace sized)
+                torch.cuda.synchronize()
+                per = time_launches(torch, lambda: prop.propagate(prec, out=U), 1, 0, flush)
+            else:
+                per = time_launches(torch, lambda: prop.propagate(prec, out=U), 3, 1, flush)
             ms = statistics.median(per)
-            rate = n / (ms * 1e-3)
-            row = {"d": d, "prec": prec, "n_steps": n, "ms": ms, "steps_per_s": rate,
-                   "ms_for_80000": ms * n1 / n, "extrapolated": n != n1}
+            rate = n1 / (ms * 1e-3)
+            st = prop.stats()
+            row = {"d": d, "padded": pad_dim(d), "prec": prec, "n_steps": n1, "ms": ms,
+                   "steps_per_s": rate, "timed_calls": len(per), "product_backends": st["product_backends"],
+                   "algorithmic_tflops": flops_per_launch(st) / (ms * 1e-3) / 1e12}
             results["e1"].append(row)
-            print(json.dumps({"e1": row}), flush=True)
+            emit("e1", row)
 
     # ---- E3: run time vs N, end to end from host memory, against the oracle
     grid = (1, 10, 100, 1000, 10000, 100000, 1000000)
@@ -684,7 +710,7 @@ def run_scaling(args):
                 rate = n / sec
                 row = {"d": d, "prec": prec, "n_steps": n, "seconds": sec}
                 results["e3_gpu"].append(row)
-                print(json.dumps({"e3_gpu": row}), flush=True)
+                emit("e3_gpu", row)
     prop.close()
 
     # CPU side: the FP64 oracle on one host core, in a fresh process, within ~10 s per size
@@ -700,7 +726,7 @@ def run_scaling(args):
         for dd, n, sec in json.loads(r.stdout.strip().splitlines()[-1]):
             row = {"d": dd, "n_steps": n, "seconds": sec, "cores": 1}
             results["e3_cpu"].append(row)
-            print(json.dumps({"e3_cpu": row}), flush=True)
+            emit("e3_cpu", row)
 
     # crossover (FP64): first N on the grid where the GPU call beats the oracle, log-log
     # interpolated between the neighbouring grid points
@@ -722,14 +748,68 @@ def run_scaling(args):
                     val = {"n_steps": math.exp(x), "between": [n0, n]}
                 break
         cross[d] = val
-    print(json.dumps({"scaling_summary": {"crossover_fp64": cross, "input": "random_problem(d, 2, N, midpoint, "
-                                          "g_norm=0.3), GUE drift and controls", "cpu": "FP64 oracle, one core"}}))
+    emit("scaling_summary", {"crossover_fp64": cross, "input": "random_problem(d, 2, N, midpoint, g_norm=0.3), "
+                                                            "GUE drift and controls", "cpu": "FP64 oracle, one core"})
+    record.close()
+
+
+def pad_dim(d: int) -> int:
+    """Padded dimension the library runs d at (next power of two, at least 2)."""
+    p = 2
+    while p < d:
+        p *= 2
+    return p
+
+
+def scaling_report(path: str) -> str:
+    """Markdown tables (run time vs d; run time vs N with the CPU oracle) of a --scaling record."""
+    rows = [json.loads(line) for line in open(path) if line.strip()]
+    e1 = [r["e1"] for r in rows if "e1" in r]
+    g3 = [r["e3_gpu"] for r in rows if "e3_gpu" in r]
+    c3 = [r["e3_cpu"] for r in rows if "e3_cpu" in r]
+    summ = [r["scaling_summary"] for r in rows if "scaling_summary" in r]
+    out = []
+    dims = sorted({r["d"] for r in e1})
+    precs = [p for p in ("fp32", "fp32_tc_tf32x3", "fp64") if any(r["prec"] == p for r in e1)]
+    out.append("| d (padded) | " + " | ".join(f"{d} ({pad_dim(d)})" if pad_dim(d) != d else str(d) for d in dims) + " |")
+    out.append("|---" * (len(dims) + 1) + "|")
+    for p in precs:
+        cells = []
+        for d in dims:
+            r = [x for x in e1 if x["d"] == d and x["prec"] == p]
+            cells.append(f"{r[0]['ms']:.4g}" if r else "—")
+        out.append(f"| {p} ms | " + " | ".join(cells) + " |")
+    out.append("")
+    ns = sorted({r["n_steps"] for r in g3} | {r["n_steps"] for r in c3})
+    ds = sorted({r["d"] for r in g3})
+    head = ["N"] + [f"d={d} {p}" for d in ds for p in ("fp32", "fp64", "cpu")]
+    out.append("| " + " | ".join(head) + " |")
+    out.append("|---" * len(head) + "|")
+
+    def fmt(sec):
+        return f"{sec * 1e3:.3g} ms" if sec < 1.0 else f"{sec:.3g} s"
+
+    for n in ns:
+        cells = [f"{n:g}"]
+        for d in ds:
+            for p in ("fp32", "fp64"):
+                r = [x for x in g3 if x["d"] == d and x["prec"] == p and x["n_steps"] == n]
+                cells.append(fmt(r[0]["seconds"]) if r else "—")
+            r = [x for x in c3 if x["d"] == d and x["n_steps"] == n]
+            cells.append(fmt(r[0]["seconds"]) if r else "—")
+        out.append("| " + " | ".join(cells) + " |")
+    if summ:
+        out.append("")
+        out.append("FP64 crossover (GPU call faster than the one-core oracle): " + json.dumps(summ[-1]["crossover_fp64"]))
+    return "\n".join(out)
 
 
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.scaling_report:
+        print(scaling_report(args.scaling_out))
     elif args.scaling:
         run_scaling(args)
     else:
