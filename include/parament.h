@@ -87,16 +87,17 @@ typedef enum {
  *        cores: every FP32 operand split into two round-to-nearest TF32 terms,
  *        three MMAs per real product (hi*hi + hi*lo + lo*hi), FP32 accumulation
  *        with a fresh accumulator per k-chunk; FP64 norm bound and FP64 top
- *        tree as in FP32.  d in 17..128: tcgen05 with tensor-memory
+ *        tree as in FP32.  d in 17..256: tcgen05 with tensor-memory
  *        accumulators (d <= 64: working matrices in shared memory, the four real
- *        products of a complex product in one M = 128 MMA chain); d in 129..256:
- *        mma.sync.  d <= 16: PARAMENT_ERR_UNSUPPORTED.
- *        parament_stats.product_backends names the code that ran.
+ *        products of a complex product in one M = 128 MMA chain; d = 129..256:
+ *        four 128 x 128 output blocks per product).  d <= 16:
+ *        PARAMENT_ERR_UNSUPPORTED.  parament_stats.product_backends names the
+ *        code that ran.
  *  FP32_TC_BF16X3: FP32 with every operand split into three round-to-nearest
  *        BF16 terms (x = b0 + b1 + b2, 24 significant bits) and the six products
  *        b0 b0 + b0 b1 + b1 b0 + b0 b2 + b1 b1 + b2 b0 per real product on the
  *        tensor cores (tcgen05 kind::f16), FP32 accumulation with a fresh
- *        accumulator per k-chunk.  d in 17..128: tcgen05; d <= 16 or d > 128:
+ *        accumulator per k-chunk.  d in 17..256: tcgen05; d <= 16:
  *        PARAMENT_ERR_UNSUPPORTED.
  */
 typedef enum {
@@ -171,7 +172,7 @@ typedef struct {
 /* product back-ends reported in parament_stats.product_backends (a batched call ORs the
    back-ends of its dimension classes) */
 #define PARAMENT_BACKEND_CUDA_CORES 0x1u /* FP32 / FP64 fused multiply-adds */
-#define PARAMENT_BACKEND_MMA_SYNC 0x2u   /* warp-level mma.sync TF32 tensor-core instructions */
+#define PARAMENT_BACKEND_MMA_SYNC 0x2u   /* warp-level mma.sync instructions (no path of this build uses them) */
 #define PARAMENT_BACKEND_TCGEN05 0x4u    /* tcgen05.mma with tensor-memory accumulators */
 
 #define PARAMENT_DEV_NONFINITE_NORM 0x1u /* a slice's norm bound was NaN/Inf */

@@ -1122,8 +1122,6 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec) 
     const bool tc_prec = prec == PARAMENT_PREC_FP32_TC_TF32X3 || prec == PARAMENT_PREC_FP32_TC_BF16X3;
     if (tc_prec && ctx->dpad <= kMaxSmallDim)
         return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "tensor-core products are used for d > %d only", kMaxSmallDim);
-    if (prec == PARAMENT_PREC_FP32_TC_BF16X3 && ctx->dpad > 128)
-        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "split-BF16x3 products are built for d <= 128");
     if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32 && !tc_prec)
         return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "unknown precision %d", (int)prec);
     DeviceGuard guard(ctx->device);

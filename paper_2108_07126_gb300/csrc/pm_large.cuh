@@ -48,10 +48,8 @@ template <typename Real, int D> struct LGeo {
     static constexpr size_t PANEL_BYTES = (size_t)2 * (AS + BS) * sizeof(C);  // double-buffered
 };
 
-template <int D> struct TcGeo;
-
-// TCM: 0 = CUDA-core products, 1 = 3xTF32 with mma.sync, 2 = 3xTF32 with tcgen05 (D = 128),
-// 3 = split BF16x3 with tcgen05 (D = 128), 4 / 5 = 3xTF32 / split BF16x3 with tcgen05 in the
+// TCM: 0 = CUDA-core products, 2 = 3xTF32 with tcgen05 (D = 128, 256: 128 x 128 output blocks),
+// 3 = split BF16x3 with tcgen05 (D = 128, 256), 4 / 5 = 3xTF32 / split BF16x3 with tcgen05 in the
 // shared-memory body of pm_tc_small.cuh (D = 32, 64)
 template <int TCM> __host__ __device__ constexpr int tcm_format() { return (TCM == 3 || TCM == 5) ? umma::kBF16x3 : umma::kTF32x3; }
 
@@ -60,7 +58,6 @@ __host__ __device__ inline size_t large_panel_bytes() {
     // the FP64 top tree and the tensor-core products run through the same panels
     size_t b = LGeo<Real, D>::PANEL_BYTES;
     if (LGeo<double, D>::PANEL_BYTES > b) b = LGeo<double, D>::PANEL_BYTES;
-    if (TcGeo<D>::PANEL_BYTES > b) b = TcGeo<D>::PANEL_BYTES;
     if (TCM >= 2 && umma::kSmemBytes > b) b = umma::kSmemBytes;
     return b;
 }
@@ -167,156 +164,6 @@ __device__ void cta_mm(const typename Cx<Real>::T *__restrict__ A, const typenam
     __syncthreads();
 }
 
-// ---------------------------------------------------------------- tensor-core product (3xTF32)
-//
-// FP32 complex product on the tensor cores with FP32 accuracy: every operand
-// x = hi + lo with hi = tf32(x), lo = tf32(x - hi) (Ootomo & Yokota's split),
-// x*y ~ hi_x hi_y + hi_x lo_y + lo_x hi_y, accumulated in FP32.  The complex
-// product takes four real products (Re = Re Re - Im Im, Im = Re Im + Im Re),
-// so 12 m16n8k8 TF32 MMAs per 16x8x8 complex tile step.
-template <int D> struct TcTile;
-template <> struct TcTile<32> { static constexpr int PASS = 1, WM = 2, WN = 4; };
-template <> struct TcTile<64> { static constexpr int PASS = 1, WM = 2, WN = 4; };
-template <> struct TcTile<128> { static constexpr int PASS = 2, WM = 2, WN = 4; };
-template <> struct TcTile<256> { static constexpr int PASS = 8, WM = 2, WN = 4; };
-
-template <int D> struct TcGeo {
-    static constexpr int PASS = TcTile<D>::PASS, WM = TcTile<D>::WM, WN = TcTile<D>::WN;
-    static constexpr int RBAND = D / PASS, WTM = RBAND / WM, WTN = D / WN;
-    static constexpr int MT = WTM / 16, NT = WTN / 8;
-    static constexpr int KP = 16, ALD = KP + 4, BLD = D + 4;
-    static constexpr int AS = RBAND * ALD, BS = KP * BLD;
-    static constexpr size_t PANEL_BYTES = (size_t)2 * (AS + BS) * sizeof(float2);
-    static_assert(WM * WN * 32 == kLargeThreads && MT >= 1 && NT >= 1, "warp tiling");
-};
-
-// round-to-nearest TF32 bits of x, ties away from zero (half a unit of the 10-bit mantissa added
-// to the magnitude bits, the 13 low bits cleared; finite inputs only)
-__device__ __forceinline__ unsigned tf32_rna(float x) { return (__float_as_uint(x) + 0x1000u) & 0xFFFFE000u; }
-
-__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
-    hi = tf32_rna(x);
-    lo = tf32_rna(x - __uint_as_float(hi));
-}
-
-__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-// d += hi_a hi_b + hi_a lo_b + lo_a hi_b
-__device__ __forceinline__ void mma3(float (&d)[4], const unsigned (&ah)[4], const unsigned (&al)[4],
-                                     const unsigned (&bh)[2], const unsigned (&bl)[2]) {
-    mma_tf32(d, al, bh);
-    mma_tf32(d, ah, bl);
-    mma_tf32(d, ah, bh);
-}
-
-template <int D>
-__device__ void cta_mm_tc(const float2 *__restrict__ A, const float2 *__restrict__ B, float2 *__restrict__ Cout,
-                          unsigned char *panels) {
-    using G = TcGeo<D>;
-    constexpr int KP = G::KP, ALD = G::ALD, BLD = G::BLD, RBAND = G::RBAND, MT = G::MT, NT = G::NT;
-    float2 *As[2] = {(float2 *)panels, (float2 *)panels + G::AS};
-    float2 *Bs[2] = {(float2 *)panels + 2 * G::AS, (float2 *)panels + 2 * G::AS + G::BS};
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp / G::WN, wn = warp % G::WN;
-    const int gq = lane >> 2, tq = lane & 3;  // group id, thread in group (fragment layout)
-
-    for (int pass = 0; pass < G::PASS; ++pass) {
-        const int row0 = pass * RBAND;
-        auto load = [&](int buf, int k0) {
-            for (int e = tid; e < RBAND * KP / 2; e += kLargeThreads) {
-                const int r = e / (KP / 2), c = (e % (KP / 2)) * 2;
-                cp_async16(As[buf] + r * ALD + c, A + (size_t)(row0 + r) * D + k0 + c);
-            }
-            for (int e = tid; e < KP * D / 2; e += kLargeThreads) {
-                const int r = e / (D / 2), c = (e % (D / 2)) * 2;
-                cp_async16(Bs[buf] + r * BLD + c, B + (size_t)(k0 + r) * D + c);
-            }
-            cp_async_commit();
-        };
-        float accr[MT][NT][4], acci[MT][NT][4];
-#pragma unroll
-        for (int i = 0; i < MT; ++i)
-#pragma unroll
-            for (int j = 0; j < NT; ++j)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) accr[i][j][v] = acci[i][j][v] = 0.f;
-        load(0, 0);
-        for (int kp = 0; kp < D / KP; ++kp) {
-            const int buf = kp & 1;
-            if (kp + 1 < D / KP) {
-                load(buf ^ 1, (kp + 1) * KP);
-                cp_async_wait_one();
-            } else {
-                cp_async_wait_all();
-            }
-            __syncthreads();
-            const float2 *a_s = As[buf], *b_s = Bs[buf];
-#pragma unroll
-            for (int kk = 0; kk < KP; kk += 8) {
-                unsigned arh[MT][4], arl[MT][4], aih[MT][4], ail[MT][4], nih[MT][4], nil[MT][4];
-#pragma unroll
-                for (int i = 0; i < MT; ++i) {
-                    const int r0 = wm * G::WTM + i * 16 + gq;
-                    const float2 v0 = a_s[r0 * ALD + kk + tq], v1 = a_s[(r0 + 8) * ALD + kk + tq];
-                    const float2 v2 = a_s[r0 * ALD + kk + tq + 4], v3 = a_s[(r0 + 8) * ALD + kk + tq + 4];
-                    const float re[4] = {v0.x, v1.x, v2.x, v3.x}, im[4] = {v0.y, v1.y, v2.y, v3.y};
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) {
-                        split_tf32(re[v], arh[i][v], arl[i][v]);
-                        split_tf32(im[v], aih[i][v], ail[i][v]);
-                        nih[i][v] = aih[i][v] ^ 0x80000000u;  // -Im A, exact
-                        nil[i][v] = ail[i][v] ^ 0x80000000u;
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < NT; ++j) {
-                    const int n = wn * G::WTN + j * 8 + gq;
-                    const float2 w0 = b_s[(kk + tq) * BLD + n], w1 = b_s[(kk + tq + 4) * BLD + n];
-                    unsigned brh[2], brl[2], bih[2], bil[2];
-                    split_tf32(w0.x, brh[0], brl[0]);
-                    split_tf32(w1.x, brh[1], brl[1]);
-                    split_tf32(w0.y, bih[0], bil[0]);
-                    split_tf32(w1.y, bih[1], bil[1]);
-#pragma unroll
-                    for (int i = 0; i < MT; ++i) {
-                        // each k8 step accumulates in fresh MMA registers; the running sums are
-                        // kept with round-to-nearest FP32 adds (the MMA accumulator truncates)
-                        float tr[4] = {0.f, 0.f, 0.f, 0.f}, ti[4] = {0.f, 0.f, 0.f, 0.f};
-                        mma3(tr, arh[i], arl[i], brh, brl);  // + Re A Re B
-                        mma3(tr, nih[i], nil[i], bih, bil);  // - Im A Im B
-                        mma3(ti, arh[i], arl[i], bih, bil);  // + Re A Im B
-                        mma3(ti, aih[i], ail[i], brh, brl);  // + Im A Re B
-#pragma unroll
-                        for (int v = 0; v < 4; ++v) {
-                            accr[i][j][v] = __fadd_rn(accr[i][j][v], tr[v]);
-                            acci[i][j][v] = __fadd_rn(acci[i][j][v], ti[v]);
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-        }
-#pragma unroll
-        for (int i = 0; i < MT; ++i)
-#pragma unroll
-            for (int j = 0; j < NT; ++j) {
-                const int r = row0 + wm * G::WTM + i * 16 + gq;
-                const int c = wn * G::WTN + j * 8 + 2 * tq;
-                Cout[(size_t)r * D + c] = make_float2(accr[i][j][0], acci[i][j][0]);
-                Cout[(size_t)r * D + c + 1] = make_float2(accr[i][j][1], acci[i][j][1]);
-                Cout[(size_t)(r + 8) * D + c] = make_float2(accr[i][j][2], acci[i][j][2]);
-                Cout[(size_t)(r + 8) * D + c + 1] = make_float2(accr[i][j][3], acci[i][j][3]);
-            }
-    }
-    __syncthreads();
-}
-
 // Cout = A * B for D x D complex64 matrices already in shared memory (row stride D), by the
 // whole block: thread (ty, tx) = (tid / 16, tid % 16) owns rows ty + 16 r and the TC consecutive
 // columns TC tx .. TC tx + TC - 1.  Per pair of k the A reads are two broadcast rows per warp
@@ -368,18 +215,29 @@ __device__ __forceinline__ void smem_mm(const float2 *__restrict__ A, const floa
     __syncthreads();
 }
 
-// the complex product used by the large kernel: CUDA cores, or 3xTF32 on the tensor cores
-// (FP32 only): mma.sync (TCM = 1) or tcgen05 with tensor-memory accumulators (TCM = 2, D = 128)
+// the complex product used by the large kernel: CUDA cores, or tcgen05 with tensor-memory
+// accumulators (FP32 only; TCM = 2 3xTF32, 3 split BF16x3): D = 128 in one 128 x 128 block, D = 256
+// in four 128 x 128 output blocks over K = 256
 template <typename Real, int D, int TCM>
 __device__ __forceinline__ void large_mm(const typename Cx<Real>::T *A, const typename Cx<Real>::T *B,
                                          typename Cx<Real>::T *Cout, unsigned char *panels, umma::Ctx *uc) {
-    if constexpr (TCM == 2 && D == 128 && std::is_same<Real, float>::value)
-        umma::cmul128<umma::kTF32x3>(A, B, Cout, panels, *uc);
-    else if constexpr (TCM == 3 && D == 128 && std::is_same<Real, float>::value)
-        umma::cmul128<umma::kBF16x3>(A, B, Cout, panels, *uc);
-    else if constexpr (TCM >= 1 && std::is_same<Real, float>::value) cta_mm_tc<D>(A, B, Cout, panels);
-    else if constexpr (large_resident<Real, D, TCM>()) smem_mm<D>(A, B, Cout);
-    else cta_mm<Real, D>(A, B, Cout, panels);
+    if constexpr ((TCM == 2 || TCM == 3) && std::is_same<Real, float>::value) {
+        constexpr int F = TCM == 3 ? umma::kBF16x3 : umma::kTF32x3;
+        if constexpr (D == 128) {
+            umma::cmul128<F>(A, B, Cout, panels, *uc);
+        } else {
+            static_assert(D == 256, "tcgen05 block product covers D = 128 and 256");
+#pragma unroll 1
+            for (int blk = 0; blk < 4; ++blk) {
+                const int i0 = (blk >> 1) * 128, j0 = (blk & 1) * 128;
+                umma::cmul128<F, 256, 256>(A + (size_t)i0 * 256, B + j0, Cout + (size_t)i0 * 256 + j0, panels, *uc);
+            }
+        }
+    } else if constexpr (large_resident<Real, D, TCM>()) {
+        smem_mm<D>(A, B, Cout);
+    } else {
+        cta_mm<Real, D>(A, B, Cout, panels);
+    }
 }
 
 // One leaf (slices [N blk / nblk, N (blk + 1) / nblk)) of one problem by one
@@ -404,7 +262,7 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
     C *SR = ws + 3 * DD, *P0 = ws + 4 * DD, *P1 = ws + 5 * DD;
     // packed exponent: in shared memory (rows padded to D + 1, conflict-free transposed reads)
     // when the tensor-core stages leave room, else in a free scratch slot
-    constexpr bool kGpkShared = (TCM >= 2) || kResident;
+    constexpr bool kGpkShared = (TCM >= 2 && D <= 128) || kResident;  // D = 256: 263 KB, too large
     static_assert(DD % (4 * kLargeThreads) == 0, "element passes take four elements per thread and step");
     constexpr int GLD = kGpkShared ? D + 1 : D;
     const Real *packed = (const Real *)p.packed;
@@ -443,7 +301,9 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
         const int code = s_code;
         const int q = cls_q(code), rh = cls_r(code), s = cls_s(code) + p.extra_squarings;
         const Real sc = pow2neg<Real>(s);
-        Real *gpk = (TCM >= 2) ? (Real *)panels : (Real *)P0;  // resident: the free slot P0 in shared memory
+        // tensor cores (D <= 128): the idle operand stages; otherwise the free slot P0 (in shared
+        // memory for the resident bodies, in the global scratch otherwise)
+        Real *gpk = (TCM >= 2 && D <= 128) ? (Real *)panels : (Real *)P0;
 
         // packed exponent sum_b gamma_b P_b: EP groups of four entries per thread and step, the
         // basis loop unrolled, so that 4 EP independent 16-byte loads from L2 are in flight (the
@@ -674,12 +534,11 @@ __device__ __forceinline__ void large_body(const FusedParams &p, typename Cx<Rea
 }
 
 // products of the tensor-core precisions in the standalone large kernel (TC: 0 none, 1 3xTF32,
-// 2 split BF16x3): tcgen05 in the shared-memory body for D = 32, 64, tcgen05 with L2-resident
-// working matrices for D = 128, mma.sync 3xTF32 for D = 256
+// 2 split BF16x3): tcgen05 in the shared-memory body for D = 32, 64, tcgen05 with working
+// matrices in a global scratch region for D = 128, 256
 template <typename Real, int D, int TC>
 __host__ __device__ constexpr int large_tcm() {
-    return (TC == 0 || !std::is_same<Real, float>::value) ? 0
-           : (D <= 64 ? (TC == 2 ? 5 : 4) : (D == 128 ? (TC == 2 ? 3 : 2) : 1));
+    return (TC == 0 || !std::is_same<Real, float>::value) ? 0 : (D <= 64 ? (TC == 2 ? 5 : 4) : (TC == 2 ? 3 : 2));
 }
 
 // blocks per SM the large kernel is compiled for: two for the tensor-core body at D = 32

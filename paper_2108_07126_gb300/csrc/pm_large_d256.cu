@@ -5,6 +5,14 @@ namespace pm {
 
 cudaError_t large_dispatch_d256(int fp64, int integ, const FusedParams &p, void *scratch, int grid, size_t smem,
                                cudaStream_t st, int tc) {
+    if (tc == 2 && !fp64) {  // split BF16x3 on tcgen05
+        switch (integ) {
+            case kMidpoint: return launch_large<float, 256, kMidpoint, 2>(p, scratch, grid, smem, st);
+            case kGL2: return launch_large<float, 256, kGL2, 2>(p, scratch, grid, smem, st);
+            case kSimpson: return launch_large<float, 256, kSimpson, 2>(p, scratch, grid, smem, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (tc && !fp64) {
         switch (integ) {
             case kMidpoint: return launch_large<float, 256, kMidpoint, 1>(p, scratch, grid, smem, st);
@@ -31,6 +39,14 @@ int large_blocks_per_sm_d256(int fp64, int integ, size_t smem, int tc) {
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kLargeThreads, smem);
     };
+    if (tc == 2 && !fp64) {
+        switch (integ) {
+            case kMidpoint: q(large_kernel<float, 256, kMidpoint, 2>); break;
+            case kGL2: q(large_kernel<float, 256, kGL2, 2>); break;
+            case kSimpson: q(large_kernel<float, 256, kSimpson, 2>); break;
+        }
+        return e == cudaSuccess ? nb : 0;
+    }
     if (tc && !fp64) {
         switch (integ) {
             case kMidpoint: q(large_kernel<float, 256, kMidpoint, 1>); break;
@@ -56,6 +72,7 @@ cudaError_t large_prefix_d256(const double2 *leaf, int n, double2 *a, double2 *b
 
 size_t large_smem_d256(int fp64, int n_basis, int tc) {
     if (fp64) return large_smem_bytes<double, 256>(n_basis);
+    if (tc == 2) return large_smem_bytes<float, 256, large_tcm<float, 256, 2>()>(n_basis);
     return tc ? large_smem_bytes<float, 256, large_tcm<float, 256, 1>()>(n_basis) : large_smem_bytes<float, 256>(n_basis);
 }
 

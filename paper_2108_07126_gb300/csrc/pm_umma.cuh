@@ -256,13 +256,15 @@ __device__ __forceinline__ void arrive(uint64_t *bar) {
     asm volatile("{\n.reg .b64 arrst;\nmbarrier.arrive.shared::cta.b64 arrst, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// C = A B; A, B, C: 128 x 128 complex FP32, row-major, global memory (C may not alias A or B).
-// Called by all 256 threads of the block; `stages` is kSmemBytes of shared memory.  Thread
-// (warp w, lane l) owns row 32 (w % 4) + l, columns [64 (w / 4), 64 (w / 4) + 64) of Re C and Im C.
-template <int F>
+// C = A B for one 128 x 128 block of complex FP32 output: A is 128 x KDIM, B is KDIM x 128, all
+// row-major in global memory with row stride LD (C may not alias A or B).  LD = KDIM = 128 is the
+// whole d = 128 product; d = 256 takes four blocks with LD = KDIM = 256.  Called by all 256
+// threads of the block; `stages` is kSmemBytes of shared memory.  Thread (warp w, lane l) owns
+// row 32 (w % 4) + l, columns [64 (w / 4), 64 (w / 4) + 64) of Re C and Im C.
+template <int F, int LD = 128, int KDIM = 128>
 static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const float2 *__restrict__ B,
                                             float2 *__restrict__ Cout, unsigned char *stages, Ctx &cx) {
-    constexpr int NCH = 128 / KC;
+    constexpr int NCH = KDIM / KC;
     constexpr int P = Fmt<F>::PLANE, SBO = Fmt<F>::SBO;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (*(volatile int *)cx.abort) return;  // uniform: set before the last block barrier
@@ -322,7 +324,7 @@ static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const 
             const int qa = q % NA, r = (qa / NKG) * 32 + lane, kk = k0 + (qa % NKG) * VPL;
             if (q < NA) {
                 // written by this block before its last barrier: plain (coherent) loads
-                const float4 *src = reinterpret_cast<const float4 *>(A + r * 128 + kk);
+                const float4 *src = reinterpret_cast<const float4 *>(A + (size_t)r * LD + kk);
 #pragma unroll
                 for (int h = 0; h < VPL / 2; ++h) {
                     const float4 a = src[h];
@@ -331,7 +333,7 @@ static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const 
                 }
             } else if (q < NITEM) {
 #pragma unroll
-                for (int t = 0; t < VPL; ++t) v[i][t] = __ldcg(B + (kk + t) * 128 + r);
+                for (int t = 0; t < VPL; ++t) v[i][t] = __ldcg(B + (size_t)(kk + t) * LD + r);
             }
         }
     };
@@ -448,7 +450,7 @@ static __device__ __noinline__ void cmul128(const float2 *__restrict__ A, const 
         __syncthreads();
         for (int r = warp; r < 128; r += 8) {
             const float4 *src = reinterpret_cast<const float4 *>(stages + r * kCRow);
-            float4 *dst = reinterpret_cast<float4 *>(Cout + r * 128);
+            float4 *dst = reinterpret_cast<float4 *>(Cout + (size_t)r * LD);
             dst[lane] = src[lane];
             dst[lane + 32] = src[lane + 32];
         }
