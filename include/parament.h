@@ -254,9 +254,11 @@ int parament_propagate(parament_ctx *ctx, void *U_out, parament_precision prec);
  * as the upper-right block of exp([[X, Lambda], [0, X]]).  The prefixes P and suffixes S come from
  * the forward tree: leaf and block products of the forward kernel, exclusive scans over them, then
  * per leaf a forward sweep (prefixes, re-computed from checkpoints for long leaves) and a backward
- * sweep.  A Simpson end sample belongs to two slices and receives both contributions.  V: d x d in
- * the dtype of set_hamiltonians; U_out: optional U(T).  Pointers host or device.  d <= 16.
- * Errors: UNSUPPORTED for d > 16 and the tensor-core precisions; STATE before set_controls.
+ * sweep.  A Simpson end sample belongs to two slices and receives both contributions.  d <= 16:
+ * groups of lanes of one warp per leaf; d = 17..256: one thread block per leaf (FP64 Hillis-Steele
+ * scans of the leaf products for the prefixes, the suffixes, U(T) and z; block-wide products).
+ * V: d x d in the dtype of set_hamiltonians; U_out: optional U(T).  Pointers host or device.
+ * Errors: UNSUPPORTED for the tensor-core precisions; STATE before set_controls.
  */
 int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, void *grad_out, void *U_out,
                             parament_precision prec);

@@ -19,6 +19,7 @@
 #include "pm_cheb.cuh"
 #include "pm_common.cuh"
 #include "pm_grad.cuh"
+#include "pm_grad_large.cuh"
 
 namespace pm {
 #define PM_DECL_D(D)                                                                                     \
@@ -40,7 +41,10 @@ PM_DECL_D(16)
     cudaError_t large_dispatch_d##D(int, int, const FusedParams &, void *, int, size_t, cudaStream_t, int); \
     int large_blocks_per_sm_d##D(int, int, size_t, int);                                                 \
     size_t large_smem_d##D(int, int, int);                                                               \
-    cudaError_t large_prefix_d##D(const double2 *, int, double2 *, double2 *, double2 **, cudaStream_t);
+    cudaError_t large_prefix_d##D(const double2 *, int, double2 *, double2 *, double2 **, cudaStream_t);    \
+    cudaError_t grad_large_run_d##D(int, int, const double2 *, int, double2 *, double2 *, const GradParams &, \
+                                    void *, void *, int, int, cudaStream_t);                             \
+    size_t adjoint_large_smem_d##D(int);
 PM_DECL_L(32)
 PM_DECL_L(64)
 PM_DECL_L(128)
@@ -94,7 +98,7 @@ struct parament_ctx {
 
     Workspace hraw, full, packed64, packed32, bnorm, partials, tickets, counters, status, check;
     Workspace ctrl_copy, ctrl_conv, uout, bmax, cpacked64, cpacked32, cbnorm;
-    Workspace gv, gvdag, gleaf, gblock, gbpin, gpin, gz, gpbuf, gckpt, ggrad, lscratch;
+    Workspace gv, gvdag, gleaf, gblock, gbpin, gpin, gz, gpbuf, gckpt, ggrad, lscratch, gadj;
     Workspace tstage, tpsi;  // trajectory: staging of a host output, psi_0 padded (FP64)
     std::vector<double2> tpsi_host;
     // batched plan
@@ -611,6 +615,25 @@ cudaError_t large_dispatch(int Dp, int fp64, int integ, const FusedParams &p, vo
     }
     return cudaErrorInvalidValue;
 }
+cudaError_t grad_large_run(int Dp, int fp64, int integ, const double2 *leaf, int L, double2 *pre, double2 *suf,
+                           const GradParams &gp, void *scratch, void *U_out, int out_c128, int d_out, cudaStream_t st) {
+    switch (Dp) {
+        case 32: return grad_large_run_d32(fp64, integ, leaf, L, pre, suf, gp, scratch, U_out, out_c128, d_out, st);
+        case 64: return grad_large_run_d64(fp64, integ, leaf, L, pre, suf, gp, scratch, U_out, out_c128, d_out, st);
+        case 128: return grad_large_run_d128(fp64, integ, leaf, L, pre, suf, gp, scratch, U_out, out_c128, d_out, st);
+        case 256: return grad_large_run_d256(fp64, integ, leaf, L, pre, suf, gp, scratch, U_out, out_c128, d_out, st);
+    }
+    return cudaErrorInvalidValue;
+}
+size_t adjoint_large_smem(int Dp, int fp64) {
+    switch (Dp) {
+        case 32: return adjoint_large_smem_d32(fp64);
+        case 64: return adjoint_large_smem_d64(fp64);
+        case 128: return adjoint_large_smem_d128(fp64);
+        case 256: return adjoint_large_smem_d256(fp64);
+    }
+    return 0;
+}
 cudaError_t large_prefix(int Dp, const double2 *leaf, int n, double2 *a, double2 *b, double2 **x, cudaStream_t st) {
     switch (Dp) {
         case 32: return large_prefix_d32(leaf, n, a, b, x, st);
@@ -804,6 +827,7 @@ int parament_destroy(parament_ctx *ctx) {
                             &ctx->ctrl_copy, &ctx->ctrl_conv, &ctx->uout, &ctx->bmax, &ctx->cpacked64,
                             &ctx->cpacked32, &ctx->cbnorm, &ctx->gv, &ctx->gvdag, &ctx->gleaf, &ctx->gblock,
                             &ctx->gbpin, &ctx->gpin, &ctx->gz, &ctx->gpbuf, &ctx->gckpt, &ctx->ggrad, &ctx->lscratch,
+                            &ctx->gadj,
                             &ctx->bparams, &ctx->binsts, &ctx->btable, &ctx->bitems, &ctx->bfull, &ctx->bpacked,
                             &ctx->bnorms, &ctx->bpartials, &ctx->btickets, &ctx->bcounters, &ctx->bstatus,
                             &ctx->bqueue, &ctx->bscratch, &ctx->cheb, &ctx->tstage, &ctx->tpsi};
@@ -1200,8 +1224,6 @@ int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, 
     if (!V || !grad_out) return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "null V or grad_out");
     if (prec != PARAMENT_PREC_FP64 && prec != PARAMENT_PREC_FP32)
         return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "gradient precision must be FP64 or FP32");
-    if (ctx->dpad > kMaxSmallDim)
-        return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "the adjoint gradient covers d <= %d", kMaxSmallDim);
     DeviceGuard guard(ctx->device);
     const int fp64 = prec == PARAMENT_PREC_FP64;
     const int Dp = ctx->dpad, d = ctx->dim, K = ctx->K;
@@ -1234,25 +1256,45 @@ int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, 
     size_t smem = 0;
     if ((st = forward_setup(ctx, fp64, udst, p, grid, warps, smem, lpb))) return st;
     const int64_t L = (int64_t)grid * lpb;
+    const bool large = Dp > kMaxSmallDim;  // one leaf per thread block, block-level adjoint
     if ((st = ws_reserve(ctx, ctx->gleaf, (size_t)L * DD * sizeof(double2)))) return st;
-    if ((st = ws_reserve(ctx, ctx->gblock, (size_t)grid * DD * sizeof(double2)))) return st;
-    if ((st = ws_reserve(ctx, ctx->gbpin, 2 * (size_t)grid * DD * sizeof(double2)))) return st;
-    if ((st = ws_reserve(ctx, ctx->gpin, 2 * (size_t)L * DD * sizeof(double2)))) return st;
     if ((st = ws_reserve(ctx, ctx->gz, 4 * sizeof(double)))) return st;
     p.leaf_out = (double2 *)ctx->gleaf.ptr;
-    p.block_out = (double2 *)ctx->gblock.ptr;
-    PM_CUDA(fused_dispatch(Dp, fp64, (int)ctx->integ, p, grid, warps, smem, ctx->stream));
-    record_launch(ctx, ctx->nb_eff, grid, warps, lpb);
+    if (large) {
+        // prefix scan over L + 1 elements (the last prefix is U(T)) and suffix scan, ping-pong each
+        if ((st = ws_reserve(ctx, ctx->gpin, (2 * (size_t)(L + 1) + 2 * (size_t)L) * DD * sizeof(double2))))
+            return st;
+        p.block_out = nullptr;
+        PM_CUDA(forward_launch(ctx, fp64, p, grid, warps, smem, 0));
+        record_launch(ctx, ctx->nb_eff, grid, warps, lpb);
+    } else {
+        if ((st = ws_reserve(ctx, ctx->gblock, (size_t)grid * DD * sizeof(double2)))) return st;
+        if ((st = ws_reserve(ctx, ctx->gbpin, 2 * (size_t)grid * DD * sizeof(double2)))) return st;
+        if ((st = ws_reserve(ctx, ctx->gpin, 2 * (size_t)L * DD * sizeof(double2)))) return st;
+        p.block_out = (double2 *)ctx->gblock.ptr;
+        PM_CUDA(fused_dispatch(Dp, fp64, (int)ctx->integ, p, grid, warps, smem, ctx->stream));
+        record_launch(ctx, ctx->nb_eff, grid, warps, lpb);
+    }
 
-    // adjoint launch geometry
-    int aw = 8;
-    while (aw > 1 && adjoint_smem(Dp, fp64, K, aw) > ctx->smem_optin) --aw;
-    const size_t asmem = adjoint_smem(Dp, fp64, K, aw);
-    if (asmem > ctx->smem_optin) return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "adjoint needs %zu B shared memory", asmem);
-    const int abps = adjoint_blocks_per_sm(Dp, fp64, (int)ctx->integ, aw, asmem);
-    if (abps <= 0) return set_err(ctx, PARAMENT_ERR_CUDA, "adjoint occupancy query failed");
-    const int agrid = abps * ctx->sm_count;
-    const int64_t TG = (int64_t)agrid * aw * fused_gpw(Dp, fp64);
+    // adjoint launch geometry: d <= 16 warp groups over a persistent grid, d > 16 one block per leaf
+    int aw = 8, agrid = 0;
+    size_t asmem = 0;
+    int64_t TG = 0;
+    if (large) {
+        asmem = adjoint_large_smem(Dp, fp64);
+        if (asmem > ctx->smem_optin)
+            return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "adjoint needs %zu B shared memory", asmem);
+        TG = L;
+    } else {
+        while (aw > 1 && adjoint_smem(Dp, fp64, K, aw) > ctx->smem_optin) --aw;
+        asmem = adjoint_smem(Dp, fp64, K, aw);
+        if (asmem > ctx->smem_optin)
+            return set_err(ctx, PARAMENT_ERR_UNSUPPORTED, "adjoint needs %zu B shared memory", asmem);
+        const int abps = adjoint_blocks_per_sm(Dp, fp64, (int)ctx->integ, aw, asmem);
+        if (abps <= 0) return set_err(ctx, PARAMENT_ERR_CUDA, "adjoint occupancy query failed");
+        agrid = abps * ctx->sm_count;
+        TG = (int64_t)agrid * aw * fused_gpw(Dp, fp64);
+    }
     const int64_t maxlen = L > 0 ? (N + L - 1) / L : 0;
     int64_t c_sub = ctx->opt_grad_subchunk > 0 ? ctx->opt_grad_subchunk : std::max<int64_t>(maxlen, 1);
     const size_t csz = 2 * rsz;  // complex element
@@ -1261,6 +1303,7 @@ int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, 
     const int64_t n_ckpt = std::max<int64_t>(1, (maxlen + c_sub - 1) / c_sub);
     if ((st = ws_reserve(ctx, ctx->gpbuf, (size_t)TG * c_sub * DD * csz))) return st;
     if ((st = ws_reserve(ctx, ctx->gckpt, (size_t)TG * n_ckpt * DD * csz))) return st;
+    if (large && (st = ws_reserve(ctx, ctx->gadj, (size_t)L * kGradSlots * DD * csz))) return st;
 
     void *gdst = grad_out;
     const bool host_g = !is_device_ptr(grad_out);
@@ -1326,7 +1369,14 @@ int parament_propagate_grad(parament_ctx *ctx, const void *V, double *loss_out, 
         std::memcpy(gp.dcls_code, tmp.cls_code, sizeof(gp.dcls_code));
     }
     if (gbytes) PM_CUDA(cudaMemsetAsync(gdst, 0, gbytes, ctx->stream));  // Simpson end points accumulate
-    PM_CUDA(grad_run(Dp, fp64, (int)ctx->integ, sp, gp, agrid, aw, asmem, ctx->stream));
+    if (large) {
+        // FP64 prefix / suffix scans, z and U(T) from them, then the block-level adjoint
+        double2 *pre = (double2 *)ctx->gpin.ptr, *suf = pre + 2 * (size_t)(L + 1) * DD;
+        PM_CUDA(grad_large_run(Dp, fp64, (int)ctx->integ, (const double2 *)ctx->gleaf.ptr, (int)L, pre, suf, gp,
+                               ctx->gadj.ptr, udst, ctx->dtype == PARAMENT_C128, d, ctx->stream));
+    } else {
+        PM_CUDA(grad_run(Dp, fp64, (int)ctx->integ, sp, gp, agrid, aw, asmem, ctx->stream));
+    }
     ctx->last.grad_subchunk = (int32_t)c_sub;
 
     if (host_g && gbytes) PM_CUDA(cudaMemcpyAsync(grad_out, gdst, gbytes, cudaMemcpyDeviceToHost, ctx->stream));

@@ -1,4 +1,5 @@
 // Instantiations of the large-dimension propagation kernel for padded dimension 128.
+#include "pm_grad_large.cuh"
 #include "pm_large.cuh"
 
 namespace pm {
@@ -74,6 +75,16 @@ size_t large_smem_d128(int fp64, int n_basis, int tc) {
     if (fp64) return large_smem_bytes<double, 128>(n_basis);
     if (tc == 2) return large_smem_bytes<float, 128, large_tcm<float, 128, 2>()>(n_basis);
     return tc ? large_smem_bytes<float, 128, large_tcm<float, 128, 1>()>(n_basis) : large_smem_bytes<float, 128>(n_basis);
+}
+
+cudaError_t grad_large_run_d128(int fp64, int integ, const double2 *leaf, int L, double2 *pre, double2 *suf,
+                               const GradParams &gp, void *scratch, void *U_out, int out_c128, int d_out,
+                               cudaStream_t st) {
+    return grad_large_run<128>(fp64, integ, leaf, L, pre, suf, gp, scratch, U_out, out_c128, d_out, st);
+}
+
+size_t adjoint_large_smem_d128(int fp64) {
+    return fp64 ? adjoint_large_smem_bytes<double, 128>() : adjoint_large_smem_bytes<float, 128>();
 }
 
 }  // namespace pm
