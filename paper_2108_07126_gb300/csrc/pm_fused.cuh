@@ -22,6 +22,7 @@
 #include <type_traits>
 
 #include "pm_common.cuh"
+#include "pm_pp16.cuh"
 
 namespace pm {
 
@@ -31,7 +32,7 @@ namespace pm {
 template <typename Real, int D> struct Tiling;
 // MAXW: most warps of a standalone fused block (its launch bound; the host picks fewer when the
 // shared memory does not fit them).
-template <> struct Tiling<float, 16> { static constexpr int LANES = 32, TR = 4, TC = 2, LD = 20, V = 2, GPAD = 16, MAXW = 16; };
+template <> struct Tiling<float, 16> { static constexpr int LANES = 32, TR = 4, TC = 2, LD = 18, V = 2, GPAD = 16, MAXW = 12; };
 template <> struct Tiling<float, 8> { static constexpr int LANES = 4, TR = 4, TC = 4, LD = 8, V = 2, GPAD = 16, MAXW = 8; };
 template <> struct Tiling<float, 4> { static constexpr int LANES = 1, TR = 4, TC = 4, LD = 4, V = 2, GPAD = 16, MAXW = 8; };
 template <> struct Tiling<float, 2> { static constexpr int LANES = 1, TR = 2, TC = 2, LD = 2, V = 2, GPAD = 16, MAXW = 8; };
@@ -53,6 +54,11 @@ template <typename Real, int D> struct Geo {
     static constexpr int GSTRIDE = NSLOT * SLOT * (int)sizeof(C) + T::GPAD;  // bytes per group
     static constexpr int NCH = DD / (4 * LANES);  // 4-entry chunks of the packed exponent per lane
     static constexpr int PS = (D >= 4) ? D + 1 : D;  // row stride of the packed exponent scratch
+    // slices assembled per pass over the shared-memory basis: the FP32 d = 16 kernel is bound by
+    // shared-memory wavefronts, and assembling two slices per pass halves the basis reads of the
+    // assembly; the second packed exponent waits in a buffer of XB bytes per group
+    static constexpr int APASS = (sizeof(Real) == 4 && D == 16) ? 2 : 1;
+    static constexpr int XB = APASS == 2 ? ((D * PS * (int)sizeof(Real) + 15) & ~15) : 0;
     static_assert(LANES == RBN * CBW, "tiling must cover the matrix");
     static_assert(NCH >= 1 && NCH * 4 * LANES == DD, "assembly chunks must cover the matrix");
     static_assert(TC % V == 0 && LD % V == 0, "vector accesses must stay aligned");
@@ -62,7 +68,7 @@ template <typename Real, int D> struct Geo {
 template <typename Real, int D>
 __host__ __device__ inline size_t warp_ws_bytes(int n_basis) {
     using G = Geo<Real, D>;
-    size_t b = (size_t)G::GPW * G::GSTRIDE + (size_t)n_basis * 32 * sizeof(Real) + 32 * sizeof(int);
+    size_t b = (size_t)G::GPW * (G::GSTRIDE + G::XB) + (size_t)n_basis * 32 * sizeof(Real) + 32 * sizeof(int);
     return (b + 15) & ~(size_t)15;
 }
 
@@ -274,6 +280,12 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
     using C = typename G::C;
     constexpr int LANES = G::LANES, GPW = G::GPW, TR = G::TR, TC = G::TC, LD = G::LD, DD = G::DD;
     constexpr int SLOT = G::SLOT, NCH = G::NCH, PS = G::PS;
+    constexpr int AP = EXPM == 2 ? 1 : G::APASS;  // slices assembled per pass over the basis
+    // FP32 d = 16 Taylor path: the products run on packed two-wide FMAs (pm_pp16.cuh) with the
+    // working matrices in its row / column layouts; the leaf product is kept in the column layout
+    // and converted to the slot layout of the tree after the last slice of the leaf
+    constexpr bool PP = std::is_same<Real, float>::value && D == 16 && EXPM == 0;
+    static_assert(!PP || G::SLOT * (int)sizeof(C) >= pp16::MAT_BYTES, "a slot holds one pp16 matrix");
 
     __shared__ int s_second;
 
@@ -291,7 +303,8 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
     unsigned char *wbase = smem + boff + (size_t)warp * wsb;
     C *slots = (C *)(wbase + (size_t)g * G::GSTRIDE);
     C *S1 = slots, *S2 = slots + SLOT, *S3 = slots + 2 * SLOT, *SR = slots + 3 * SLOT;
-    Real *gam = (Real *)(wbase + (size_t)GPW * G::GSTRIDE);
+    Real *xpk = (Real *)(wbase + (size_t)GPW * G::GSTRIDE + (size_t)g * G::XB);  // second packed exponent
+    Real *gam = (Real *)(wbase + (size_t)GPW * (G::GSTRIDE + G::XB));
     int *cls = (int *)(gam + (size_t)nb * 32);
 
     // ---- basis and its norms into shared memory
@@ -323,7 +336,19 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
                     t[r][c] = Cx<Real>::make(i == jj ? Real(1) : Real(0), Real(0));
                 }
             }
-        st_tile<Real, D>(SR, rb, cb, t);
+        if constexpr (PP) {
+            pp16::Tile id;
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    id.re[r][c] = pp16::orow(lane >> 3, r) == 2 * (lane & 7) + c ? 1.f : 0.f;
+                    id.im[r][c] = 0.f;
+                }
+            pp16::st_col(reinterpret_cast<float4 *>(SR), lane >> 3, lane & 7, id);
+        } else {
+            st_tile<Real, D>(SR, rb, cb, t);
+        }
     }
     __syncthreads();
 
@@ -388,35 +413,178 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
             const int q = cls_q(code), rh = cls_r(code);
             const int s = cls_s(code) + p.extra_squarings;
 
-            // -- exponent in packed form: lane owns chunks gl + LANES * t of 4 entries
-            Real *gpk = (Real *)S2;  // scratch until X^2 is formed
-            {
-                Real acc[NCH][4];
+            // -- exponent in packed form: lane owns chunks gl + LANES * t of 4 entries.  With two
+            //    slices per pass (AP = 2; not in trajectory mode, whose registers are full) the even
+            //    slice of a pair also assembles the odd one into xpk, and the odd slice starts there.
+            const bool second = AP == 2 && (rr & 1);
+            const bool both = AP == 2 && !(rr & 1) && rr + 1 < nr;
+            const Real *gpk = second ? xpk : (const Real *)S2;  // S2 is scratch until X^2 is formed
+            if (!second) {
+                Real acc[NCH][4], acc2[AP == 2 ? NCH : 1][4];
 #pragma unroll
                 for (int t = 0; t < NCH; ++t)
 #pragma unroll
                     for (int u = 0; u < 4; ++u) acc[t][u] = Real(0);
                 const Real *gcol = gam + g * LANES + rr;
-                for (int e = 0; e < nb; ++e) {
-                    const Real ge = gcol[e * 32];
-                    const Real *Pe = basis + e * DD;
+                bool two = false;
+                if constexpr (AP == 2) two = both;
+                if (two) {
 #pragma unroll
-                    for (int t = 0; t < NCH; ++t) {
-                        Real v[4];
-                        ld4<Real>(Pe + 4 * (gl + LANES * t), v);
+                    for (int t = 0; t < (int)(sizeof(acc2) / sizeof(acc2[0])); ++t)
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) acc[t][u] = fma(ge, v[u], acc[t][u]);
+                        for (int u = 0; u < 4; ++u) acc2[t][u] = Real(0);
+                    for (int e = 0; e < nb; ++e) {
+                        Real ge[2];  // slices rr and rr + 1 (rr is even: one 8-byte load)
+                        if constexpr (AP == 2) {
+                            const float2 gv = *reinterpret_cast<const float2 *>(gcol + e * 32);
+                            ge[0] = gv.x;
+                            ge[1] = gv.y;
+                        }
+                        const Real *Pe = basis + e * DD;
+#pragma unroll
+                        for (int t = 0; t < NCH; ++t) {
+                            Real v[4];
+                            ld4<Real>(Pe + 4 * (gl + LANES * t), v);
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                acc[t][u] = fma(ge[0], v[u], acc[t][u]);
+                                if constexpr (AP == 2) acc2[t][u] = fma(ge[1], v[u], acc2[t][u]);
+                            }
+                        }
+                    }
+                } else {
+                    for (int e = 0; e < nb; ++e) {
+                        const Real ge = gcol[e * 32];
+                        const Real *Pe = basis + e * DD;
+#pragma unroll
+                        for (int t = 0; t < NCH; ++t) {
+                            Real v[4];
+                            ld4<Real>(Pe + 4 * (gl + LANES * t), v);
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) acc[t][u] = fma(ge, v[u], acc[t][u]);
+                        }
                     }
                 }
+                Real *dst = (Real *)S2;
 #pragma unroll
                 for (int t = 0; t < NCH; ++t)
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int pos = 4 * (gl + LANES * t) + u;
-                        gpk[(pos / D) * PS + (pos % D)] = acc[t][u];
+                        dst[(pos / D) * PS + (pos % D)] = acc[t][u];
+                        if constexpr (AP == 2)
+                            if (two) xpk[(pos / D) * PS + (pos % D)] = acc2[t][u];
                     }
             }
             __syncwarp();
+
+            if constexpr (PP) {
+                // -- packed-pair products (pm_pp16.cuh).  Slots: S1 = R(X), S2 = R(X^2), S3 = R(X^3);
+                //    the Horner / squaring operand T takes the two slots that the powers leave free
+                //    (Ta: C(T), Tb: R(T)); SR holds C(R) of the leaf product.
+                using pp16::Tile;
+                const int pa = lane >> 3, pb = lane & 7;
+                float4 *M1 = reinterpret_cast<float4 *>(S1), *M2 = reinterpret_cast<float4 *>(S2);
+                float4 *M3 = reinterpret_cast<float4 *>(S3), *MR = reinterpret_cast<float4 *>(SR);
+                const Real sc = pow2neg<Real>(s);
+                Tile x1, x2, tt;
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 2; ++c) {
+                        const int i = pp16::orow(pa, r), jj = 2 * pb + c;
+                        const Real va = gpk[i * PS + jj], vb = gpk[jj * PS + i];
+                        const Real re = (i <= jj) ? va : vb;
+                        const Real im = (i > jj) ? va : ((i < jj) ? -vb : Real(0));
+                        x1.re[r][c] = im * sc;
+                        x1.im[r][c] = -re * sc;
+                        x2.re[r][c] = x2.im[r][c] = 0.f;
+                    }
+                pp16::st_row(M1, pa, pb, x1);
+                __syncwarp();
+
+                const Real atop = coef<Real>(p, q * rh);
+                const float4 *Mq = (q == 1) ? M1 : ((q == 2) ? M2 : M3);
+                float4 *Ta = (q == 1) ? M2 : M1;
+                float4 *Tb = (q == 3) ? M2 : M3;
+                auto add_block = [&](int bl) {
+                    const Real a0 = coef<Real>(p, q * bl);
+                    const Real a1 = (q >= 2) ? coef<Real>(p, q * bl + 1) : Real(0);
+                    const Real a2 = (q >= 3) ? coef<Real>(p, q * bl + 2) : Real(0);
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            const bool diag = pp16::orow(pa, r) == 2 * pb + c;
+                            Real vr = tt.re[r][c] + (diag ? a0 : Real(0)), vi = tt.im[r][c];
+                            if (q >= 2) {
+                                vr = fma(a1, x1.re[r][c], vr);
+                                vi = fma(a1, x1.im[r][c], vi);
+                            }
+                            if (q >= 3) {
+                                vr = fma(a2, x2.re[r][c], vr);
+                                vi = fma(a2, x2.im[r][c], vi);
+                            }
+                            tt.re[r][c] = vr;
+                            tt.im[r][c] = vi;
+                        }
+                };
+                auto start_horner = [&](const Tile &top) {
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 2; ++c) {
+                            tt.re[r][c] = atop * top.re[r][c];
+                            tt.im[r][c] = atop * top.im[r][c];
+                        }
+                    add_block(rh - 1);
+                };
+                const int n_pow = q - 1, n_hor = rh - 1;
+                const int n_prod = n_pow + n_hor + s + 1;
+                int bl = rh - 1;
+                if (n_pow == 0) start_horner(x1);
+                for (int pi = 0; pi < n_prod; ++pi) {
+                    Tile acc;
+                    if (pi < n_pow) {
+                        // X^2 = X X, X^3 = X^2 X: B = X from its row layout (anti-Hermitian)
+                        pp16::mm<true>(pi == 0 ? M1 : M2, M1, pa, pb, acc);
+                        if (pi == 0) {
+                            x2 = acc;
+                            pp16::st_row(M2, pa, pb, acc);
+                        } else {
+                            pp16::st_row(M3, pa, pb, acc);
+                        }
+                        if (pi == n_pow - 1) start_horner(acc);
+                        __syncwarp();
+                        continue;
+                    }
+                    // T in the layouts the next product reads: C(T) as the right operand of a
+                    // Horner step or squaring, R(T) as the left operand of a squaring or the leaf
+                    const bool leafp = pi == n_prod - 1;
+                    const bool horner = pi < n_pow + n_hor;
+                    if (!leafp) pp16::st_col(Ta, pa, pb, tt);
+                    if (!horner) pp16::st_row(Tb, pa, pb, tt);
+                    __syncwarp();
+                    //   T <- X^q T + B_b, T <- T T, R <- T R (later slice on the left)
+                    pp16::mm<false>(horner ? Mq : Tb, leafp ? MR : Ta, pa, pb, acc);
+                    __syncwarp();
+                    if (leafp) {
+                        pp16::st_col(MR, pa, pb, acc);
+                        __syncwarp();
+                    } else {
+                        tt = acc;
+                        if (horner) add_block(--bl);
+                    }
+                }
+                if (gl == 0 && (t0 + rr) < len) {
+                    n_exp += (unsigned long long)((q - 1) + (rh - 1) + s);
+                    n_tree += 1;
+                    m_max = max(m_max, cls_m(code));
+                    s_max = max(s_max, s);
+                }
+                continue;
+            }
+
 
             if constexpr (EXPM == 1) {
                 // -- Chebyshev (Sec. 2.1, Algorithm 1): X = G / beta, D_k = a_k I + 2 X D_{k+1} - D_{k+2},
@@ -609,6 +777,21 @@ __device__ __forceinline__ void fused_body(const FusedParams &p, int blk, int nb
             }
         }
         __syncwarp();
+    }
+
+    // packed-pair path: the leaf product from C(R) into the slot layout of the tree
+    if constexpr (PP) {
+        if (active_warp) {
+            pp16::Tile t;
+            pp16::ld_col(reinterpret_cast<const float4 *>(SR), lane >> 3, lane & 7, t);
+            __syncwarp();
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 2; ++c)
+                    SR[pp16::orow(lane >> 3, r) * LD + 2 * (lane & 7) + c] = make_float2(t.re[r][c], t.im[r][c]);
+            __syncwarp();
+        }
     }
 
     // trajectory mode: the forward pass already combined the leaves and recorded statistics
