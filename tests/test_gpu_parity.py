@@ -1,11 +1,10 @@
 """Parity of the CUDA propagator with the FP64 oracle, through the C ABI.
 
-Tolerances.  FP64 path: max-entry |U - U_oracle| <= 1e-11.  FP32 path: each
-slice contributes a rounding error of a few units of u = 2^-24 per entry
-times the dimension (assembly, Taylor polynomial, leaf product), and the N
-slice errors add up like a random walk, so the tests allow
-20 * u * d * sqrt(N) (plus the same for the oracle-side truncation of the
-inputs to float32), measured values are reported by the benchmark.
+Tolerances (tests/tolerances.py).  FP64 path: max-entry |U - U_oracle| <= 1e-11.  FP32
+path, against the oracle on the float32-rounded inputs: each slice adds a few units of
+u = 2^-24 of rounding per entry (assembly, Taylor polynomial, squarings, leaf product) and the
+N slice errors add like a random walk, so the bound is 24 u sqrt(N) + 16 u; the tensor-core
+forms get twice that.
 """
 
 import numpy as np
@@ -92,6 +91,23 @@ def test_norm_range_uses_degree_and_squaring(prop, d, g_norm):
     if g_norm >= 9.0:
         assert st["max_squarings"] >= 3
     assert st["device_status"] == 0
+
+
+@pytest.mark.parametrize("integrator", ["midpoint", "magnus4_gl2"])
+@pytest.mark.parametrize("g_norm", [1e-4, 0.05, 0.6, 2.5, 9.0, 40.0])
+def test_fp32_d16_norm_range(prop, integrator, g_norm):
+    """FP32 d = 16 (packed two-wide FMA products) through every Paterson-Stockmeyer shape:
+    tiny exponents take degree 1 or 2 (no power or one power of X), large ones squarings, whose
+    rounding grows with the norm."""
+    prob = wl.random_problem(16, 2, 19, integrator, seed=320 + int(10 * g_norm), g_norm=g_norm)
+    U = run(prop, prob, "fp32")
+    check(np.max(np.abs(U - ref32(prob))), tol32(16, 19) * max(1.0, g_norm))
+    st = prop.stats()
+    assert st["tree_products"] == 19 and st["device_status"] == 0
+    if g_norm <= 1e-4:
+        assert st["max_degree"] <= 2
+    if g_norm >= 9.0:
+        assert st["max_squarings"] >= 2
 
 
 def test_empty_run_is_identity(prop):
