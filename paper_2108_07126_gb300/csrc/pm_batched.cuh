@@ -112,6 +112,15 @@ static __device__ __noinline__ void batch_large_item(const FusedParams &p, unsig
     large_arrival_tree<Real, D>(p, ws, blk, nblk, smem);
 }
 
+// the CUDA-core D = 64 items, inlined into the kernel: most of a mixed sweep's work, and as a
+// separate function their products ran 20 % slower than in the single-problem kernel
+template <typename Real, int D, int INTEG>
+static __device__ __forceinline__ void batch_large_item_inl(const FusedParams &p, unsigned char *ws, int blk, int nblk,
+                                                            unsigned char *smem) {
+    large_body<Real, D, INTEG, 0>(p, (typename Cx<Real>::T *)ws, blk, nblk, smem, nullptr);
+    large_arrival_tree<Real, D>(p, ws, blk, nblk, smem);
+}
+
 // D = 32 / 64 on the tensor cores: the shared-memory body of pm_tc_small.cuh, then the arrival tree
 template <int D, int INTEG, int F>
 static __device__ __noinline__ void batch_tc_item(const FusedParams &p, unsigned char *ws, int blk, int nblk,
@@ -169,7 +178,7 @@ __global__ void __launch_bounds__(256, 1) batched_kernel(const BatchItem *__rest
                         break;
                     }
                 }
-                batch_large_item<Real, 64, INTEG, 0>(p, ws, w.blk, w.nblk, smem, nullptr);
+                batch_large_item_inl<Real, 64, INTEG>(p, ws, w.blk, w.nblk, smem);
                 break;
             case 128:
                 if constexpr (kTc) {
