@@ -53,7 +53,9 @@ template <typename Real, int D> struct Geo {
     static constexpr int NSLOT = 4;               // X (then Horner operand), X^2, X^3, R
     static constexpr int GSTRIDE = NSLOT * SLOT * (int)sizeof(C) + T::GPAD;  // bytes per group
     static constexpr int NCH = DD / (4 * LANES);  // 4-entry chunks of the packed exponent per lane
-    static constexpr int PS = (D >= 4) ? D + 1 : D;  // row stride of the packed exponent scratch
+    // row stride of the packed exponent scratch (FP32 d = 16: 19, fewest bank conflicts for the
+    // assembly's stores and the packed-FMA path's transposed unpack reads together)
+    static constexpr int PS = (sizeof(Real) == 4 && D == 16) ? 19 : ((D >= 4) ? D + 1 : D);
     // slices assembled per pass over the shared-memory basis: the FP32 d = 16 kernel is bound by
     // shared-memory wavefronts, and assembling two slices per pass halves the basis reads of the
     // assembly; the second packed exponent waits in a buffer of XB bytes per group
