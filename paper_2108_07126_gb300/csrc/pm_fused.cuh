@@ -16,7 +16,11 @@
 //
 // Shared-memory layout per block: the packed basis (row stride D) and its
 // norms, then per warp: GPW groups x 4 complex D x LD slots (X / Horner
-// operand, X^2, X^3, leaf product R), the coefficient tile and class tile.
+// operand, X^2, X^3, leaf product R), the second packed exponent of a pair
+// (FP32 d = 16 only), the coefficient tile and class tile.  The FP32 d = 16
+// Taylor path keeps the slots in the row / column chunk layouts of
+// pm_pp16.cuh while a leaf runs and converts the leaf product to the slot
+// layout for the tree.
 #pragma once
 
 #include <type_traits>
