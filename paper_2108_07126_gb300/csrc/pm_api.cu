@@ -1714,7 +1714,6 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
     if ((cdtype == PARAMENT_F64) != (fp64 != 0))
         return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "control dtype must match the precision in batched calls");
     const int magnus = integ != PARAMENT_MIDPOINT;
-    const int variant = (magnus ? 4 : 0) + (fp64 ? 3 : tc);
     const unsigned cuda_mask = tc ? (unsigned)ctx->opt_batch_cuda_mask : 0u;
     ctx->last_batched = true;
     if (n == 0) return PARAMENT_OK;
@@ -1730,6 +1729,15 @@ int batch_run(parament_ctx *ctx, const parament_instance *inst, int n, parament_
             (q.n_ctrl > 0 && S > 0 && !is_device_ptr(q.c)))
             return set_err(ctx, PARAMENT_ERR_INVALID_VALUE, "instance %d: batched calls take device pointers", i);
     }
+    // the tensor-core kernel only when some instance's products run on the tensor cores: with
+    // every class on the CUDA cores (the autotuner's choice for sweeps of d <= 64) the plain FP32
+    // kernel runs the same products without the tensor-memory set-up
+    bool needs_tc = false;
+    for (int i = 0; i < n && tc; ++i) {
+        const int cls = batch_tc_class(pad_dim(inst[i].dim));
+        if (cls >= 0 && !((cuda_mask >> cls) & 1u)) needs_tc = true;
+    }
+    const int variant = (magnus ? 4 : 0) + (fp64 ? 3 : (needs_tc ? tc : 0));
     const int leaf_steps = ctx->opt_batch_leaf > 0 ? (int)ctx->opt_batch_leaf : 64;
     const int items_per_sm = ctx->opt_batch_items > 0 ? (int)ctx->opt_batch_items : 32;
     const size_t csz = fp64 ? 16 : 8, rsz = fp64 ? 8 : 4;
